@@ -1,0 +1,275 @@
+/*
+ * spai.h - C ABI of the GB300 (sm_103a) SPAI-preconditioned CG library.
+ *
+ * The library solves sparse SPD systems A x = b with conjugate gradients
+ * preconditioned by a factorised sparse approximate inverse
+ *
+ *     M^-1 = G G^T + eps I                         (paper, Eq. 1)
+ *
+ * where G has the sparsity pattern of A and its values come either from the
+ * GNN forward pass of Sec. 3.2.2 (Eqs. 3-5) or from the caller.  Applying M^-1
+ * costs two sparse mat-vecs and an axpy (Sec. 3.2.1, Eq. 2); the solver is
+ * Algorithm 1 of App. A (standard PCG with the true residual recomputed every
+ * 50 iterations).
+ *
+ * Conventions for every call:
+ *  - Pointers documented as "device" must point to memory of the current CUDA
+ *    device; "host" pointers to ordinary (or pinned) host memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Work is enqueued on it; a call returns after its results are
+ *    complete unless stated otherwise.
+ *  - CSR matrices: int32 row pointers (n+1) starting at 0, int32 column
+ *    indices with strictly ascending columns in each row, no duplicates, the
+ *    diagonal present in every row and a structurally symmetric pattern
+ *    (A is SPD).  Values are float64.
+ *  - The caller owns every buffer it passes and keeps it alive and unmodified
+ *    for the duration of the call (for the server: until the request
+ *    completes).  Handles (spai_pattern, spai_precond, spai_system,
+ *    spai_server) own their own device memory and free it in *_destroy.
+ *  - Return value: SPAI_OK (0) or a negative SPAI_ERR_* code.  No C++
+ *    exception crosses this boundary.  spai_last_error() returns a message
+ *    for the calling thread's last failure.
+ *  - If the CUDA kernels of the library cannot run (no device, wrong
+ *    architecture) every compute call fails with SPAI_ERR_CUDA; there is no
+ *    CPU fallback.
+ */
+#ifndef SPAI_H
+#define SPAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----- status codes ----- */
+#define SPAI_OK                 0
+#define SPAI_ERR_INVALID       -1  /* bad argument (null pointer, bad enum, n < 0, ...) */
+#define SPAI_ERR_BAD_CSR       -2  /* CSR violates the conventions above */
+#define SPAI_ERR_SHAPE         -3  /* sizes of A, G, weights or features disagree */
+#define SPAI_ERR_CUDA          -4  /* a CUDA runtime call or kernel launch failed */
+#define SPAI_ERR_OOM           -5  /* device allocation failed */
+#define SPAI_ERR_BREAKDOWN     -6  /* PCG breakdown: d^T q <= 0 or a non-finite scalar */
+#define SPAI_ERR_NOT_CONVERGED -7  /* max_iter reached; x holds the last iterate */
+#define SPAI_ERR_TIMEOUT       -8  /* a bounded device-side wait gave up */
+#define SPAI_ERR_TOO_LARGE     -9  /* request can never fit under the server's memory cap */
+#define SPAI_ERR_NOT_FOUND    -10  /* unknown system id or ticket */
+
+/* ----- value types ----- */
+#define SPAI_F64  0
+#define SPAI_F32  1
+#define SPAI_BF16 2
+#define SPAI_F16  3
+
+/* ----- pattern kinds for G (Sec. 3.2.2 keeps A's pattern: FULL) ----- */
+#define SPAI_PATTERN_FULL  0  /* pattern of G = pattern of A (learned G) */
+#define SPAI_PATTERN_LOWER 1  /* entries with j <= i */
+#define SPAI_PATTERN_UPPER 2  /* entries with j >= i (a classical factorised SPAI: G = W^T) */
+
+/* ----- solver options ----- */
+#define SPAI_PREC_F64   0  /* everything in float64 */
+#define SPAI_PREC_MIXED 1  /* float32 inner PCG inside float64 iterative refinement */
+
+#define SPAI_CRIT_RESIDUAL 0  /* stop when ||b - A x|| <= rtol ||b|| (tables of Sec. 4.2) */
+#define SPAI_CRIT_PRECOND  1  /* Algorithm 1's own test: r^T M^-1 r <= rtol^2 r0^T M^-1 r0 */
+
+#define SPAI_MSG_LATENT 0  /* message MLP reads the latent edge state h_ij (default) */
+#define SPAI_MSG_RAW    1  /* message MLP reads the raw edge feature e_ij as Eq. 4 prints it */
+
+typedef struct {
+  int64_t n;              /* rows = columns */
+  int64_t nnz;            /* stored entries */
+  const int32_t* rowptr;  /* device, n+1 */
+  const int32_t* colidx;  /* device, nnz */
+  const void* val;        /* device, nnz values of type `dtype` */
+  int32_t dtype;          /* SPAI_F64 */
+} spai_csr;
+
+typedef struct spai_pattern spai_pattern;
+typedef struct spai_precond spai_precond;
+typedef struct spai_system spai_system;
+typedef struct spai_server spai_server;
+
+/* GNN weights (Sec. 3.2.2; sizes of Sec. 4.1).  `blob` is a device array of
+ * float32 holding, for every MLP in the order E_n, E_e, (f_m, f_v, f_e) per
+ * layer, D, the block [W1 (24 x fan_in, row-major), b1 (24), W2 (fan_out x 24,
+ * row-major), b2 (fan_out)].  Every MLP is Linear -> ReLU -> Linear with 24
+ * hidden units.  Fan-ins: E_n d_node, E_e 1, f_m 72 (or 49 with
+ * SPAI_MSG_RAW), f_v 24, f_e 72, D 24; fan-outs 24 except D (1). */
+typedef struct {
+  const float* blob;   /* device */
+  int64_t count;       /* number of floats in blob (checked) */
+  int32_t d_node;      /* node feature width, 1..16 */
+  int32_t n_layers;    /* message-passing layers L, 0..8 (paper: 4) */
+  int32_t msg_edge;    /* SPAI_MSG_LATENT or SPAI_MSG_RAW */
+} spai_gnn_weights;
+
+typedef struct {
+  double rtol;             /* target ||b - A x|| / ||b|| (paper: 1e-8) */
+  int64_t max_iter;        /* iteration cap (all inner iterations); <= 0: min(10 n, 1e6) */
+  int32_t replace_period;  /* recompute r = b - A x every this many iterations (50); 0 = never */
+  int32_t criterion;       /* SPAI_CRIT_* */
+  int32_t precision;       /* SPAI_PREC_* */
+  double inner_rtol;       /* mixed only: relative residual reduction per inner solve (<= 0: 1e-4) */
+  int32_t max_outer;       /* mixed only: cap on refinement steps (<= 0: 100) */
+  int32_t record_history;  /* nonzero: write ||r|| after every iteration into `history` */
+  double* history;         /* device, history_len doubles (history[0] = ||r_0||), may be NULL */
+  int64_t history_len;
+} spai_pcg_opts;
+
+typedef struct {
+  int64_t iters;         /* PCG iterations done (inner iterations for mixed) */
+  int32_t outer_iters;   /* refinement steps (mixed), else 0 */
+  int32_t status;        /* SPAI_OK, SPAI_ERR_NOT_CONVERGED, SPAI_ERR_BREAKDOWN, ... */
+  double true_rel_res;   /* ||b - A x|| / ||b|| in float64 at exit, computed on the device */
+  double rec_rel_res;    /* recurrence residual at exit relative to ||b|| */
+  int64_t history_written; /* entries written to opts->history */
+} spai_pcg_result;
+
+/* Fills `o` with the defaults (rtol 1e-8, replace_period 50, RESIDUAL, F64). */
+void spai_pcg_opts_default(spai_pcg_opts* o);
+
+/* Thread-local message describing the last failed call (never NULL). */
+const char* spai_last_error(void);
+
+/* Library version and the CUDA architecture the kernels were built for. */
+const char* spai_version(void);
+
+/* ------------------------------------------------------------------------ *
+ * build_pattern - sparsity pattern of G and its explicit transpose.
+ * Sec. 3.2.2: G is written on A's pattern (FULL).  LOWER/UPPER restrict it to
+ * a triangle for classical factorised inverses.  Validates A (CSR conventions
+ * above); a bad CSR returns SPAI_ERR_BAD_CSR and creates nothing.
+ * The handle stores G's CSR, G^T's CSR and perm with val_T[perm[e]] = val[e];
+ * for FULL the transposed CSR equals G's and perm[e] is the index of (j, i).
+ * ------------------------------------------------------------------------ */
+int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern** out, void* stream);
+
+/* n and nnz of G. */
+int spai_pattern_info(const spai_pattern* P, int64_t* n, int64_t* nnz_g);
+
+/* Copies the pattern to caller device buffers (any pointer may be NULL):
+ * rowptr/t_rowptr n+1 int32, colidx/t_colidx/perm nnz_g int32. */
+int spai_pattern_export(const spai_pattern* P, int32_t* rowptr, int32_t* colidx,
+                        int32_t* t_rowptr, int32_t* t_colidx, int32_t* perm, void* stream);
+
+void spai_pattern_destroy(spai_pattern* P);
+
+/* ------------------------------------------------------------------------ *
+ * gnn_precond - the GNN forward pass of Sec. 3.2.2 (Eqs. 3-5) writing G.
+ * Inputs: A (float64 CSR, device), the pattern P built from A with kind FULL,
+ * node features v (device float32, n x d_node row-major) and weights W.
+ * Edge features are A_ij / ||A|| with ||A|| = mean |A_ij| (Sec. 3.3).
+ * G is stored in `g_dtype` (F64, F32, BF16 or F16) together with G^T, and
+ * eps is the shift of Eq. 1.  Returns SPAI_ERR_SHAPE on a d_node / weight /
+ * pattern mismatch.
+ * ------------------------------------------------------------------------ */
+int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const float* node_feat,
+                     const spai_gnn_weights* W, int32_t g_dtype, double eps,
+                     spai_precond** out, void* stream);
+
+/* Preconditioner from caller-supplied values of G on P (device array of
+ * nnz_g values of type val_dtype, F64 or F32, in P's CSR order), stored in
+ * g_dtype.  Used for classical factors (FSAI, Jacobi, identity). */
+int spai_precond_from_values(const spai_pattern* P, const void* g_val, int32_t val_dtype,
+                             int32_t g_dtype, double eps, spai_precond** out, void* stream);
+
+/* Copies the stored G and G^T values, converted to `dtype` (F64 or F32), to
+ * caller device buffers of nnz_g entries (either may be NULL). */
+int spai_precond_export(const spai_precond* M, void* g_val, void* gt_val, int32_t dtype, void* stream);
+
+/* ||A|| = mean |A_ij| as computed inside gnn_precond (Sec. 3.3). */
+int spai_precond_matrix_norm(const spai_precond* M, double* norm);
+
+void spai_precond_destroy(spai_precond* M);
+
+/* ------------------------------------------------------------------------ *
+ * Systems: A prepared for repeated solves (validated, float32 copy, SpMV
+ * schedule).  `autotune` nonzero times candidate schedules on the device and
+ * keeps the fastest; the choice depends only on A, never on what else runs.
+ * ------------------------------------------------------------------------ */
+int spai_system_create(const spai_csr* A, int32_t autotune, spai_system** out, void* stream);
+
+/* Schedule chosen for the system: tile size in nonzeros and block size. */
+int spai_system_schedule(const spai_system* S, int32_t* tile_nnz, int32_t* block_threads);
+
+void spai_system_destroy(spai_system* S);
+
+/* ------------------------------------------------------------------------ *
+ * pcg_solve - Algorithm 1 (App. A) with M^-1 = G G^T + eps I (Eq. 1).
+ * b and x are device float64 arrays of n entries; x holds x0 on entry and the
+ * solution on exit.  With precision MIXED the PCG iterations run in float32
+ * (A, G, vectors) with float64 dot products, inside float64 iterative
+ * refinement on the true residual.  On SPAI_ERR_NOT_CONVERGED or
+ * SPAI_ERR_BREAKDOWN x holds the last iterate and `res` is filled.
+ * ------------------------------------------------------------------------ */
+int spai_pcg_solve(const spai_csr* A, const spai_precond* M, const double* b, double* x,
+                   const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);
+
+int spai_system_solve(spai_system* S, const spai_precond* M, const double* b, double* x,
+                      const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);
+
+/* Many systems in one persistent launch: systems advance in lockstep, each
+ * with its own scalars, and leave the work list when they converge.  Arrays
+ * have nsys entries; res[i] is filled for every system; the return value is
+ * SPAI_OK if every system converged, else the first failing status.  One
+ * system's failure does not stop the others.  All systems use the same
+ * opts (history recording is ignored). */
+int spai_pcg_solve_batched(int32_t nsys, spai_system* const* S, const spai_precond* const* M,
+                           const double* const* b, double* const* x, const spai_pcg_opts* opts,
+                           spai_pcg_result* res, void* stream);
+
+/* Same as spai_pcg_solve but b and x are HOST float64 arrays; the copies to
+ * and from the device are part of the call. */
+int spai_pcg_solve_host(const spai_csr* A, const spai_precond* M, const double* b_host,
+                        double* x_host, const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);
+
+/* ------------------------------------------------------------------------ *
+ * serve - continuous batching of solve requests on device-resident systems.
+ * Requests (b, x on the host) are queued by submit(), which never blocks;
+ * a worker thread admits them into free slots while the HBM footprint stays
+ * under hbm_cap_bytes, runs all admitted solves together in persistent
+ * launches of `chunk_iters` iterations, retires each system in the iteration
+ * it converges and admits waiting requests as slots free up.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t hbm_cap_bytes;   /* cap on the device bytes of admitted requests */
+  int32_t max_slots;       /* concurrent requests at most */
+  int32_t chunk_iters;     /* iterations per persistent launch between admissions (<= 0: 16) */
+  spai_pcg_opts opts;      /* solver options for every request (history ignored) */
+} spai_serve_cfg;
+
+typedef struct {
+  uint64_t ticket;
+  int32_t status;
+  int64_t iters;
+  int32_t outer_iters;
+  double true_rel_res;
+  double t_submit_us, t_admit_us, t_done_us;  /* host microseconds since server start */
+} spai_completion;
+
+int spai_server_create(const spai_serve_cfg* cfg, spai_server** out);
+
+/* Registers a system with its preconditioner; the server keeps references,
+ * so S and M must outlive the server. */
+int spai_server_register(spai_server* srv, spai_system* S, const spai_precond* M, int64_t* sys_id);
+
+/* Queues a request: b_host (n doubles) is read and x_host (n doubles) written
+ * before the request's completion is reported.  x starts from zero. */
+int spai_server_submit(spai_server* srv, int64_t sys_id, const double* b_host, double* x_host,
+                       uint64_t* ticket);
+
+/* Copies up to `max` finished requests into `out`; *count receives how many. */
+int spai_server_poll(spai_server* srv, spai_completion* out, int32_t max, int32_t* count);
+
+/* Waits up to timeout_ms for the request; SPAI_ERR_TIMEOUT if it did not finish. */
+int spai_server_wait(spai_server* srv, uint64_t ticket, int64_t timeout_ms, spai_completion* out);
+
+/* Stops the worker after the admitted requests finish and frees everything. */
+int spai_server_destroy(spai_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAI_H */

@@ -1,0 +1,1108 @@
+// Persistent preconditioned-CG engine.
+//
+// Algorithm 1 (App. A) with M^-1 = G G^T + eps I (Eq. 1) applied as two row
+// gathers (Eq. 2: first t = G^T r over the explicit transposed CSR, then
+// s = G t + eps r).  One cooperative kernel runs many iterations (and many
+// independent systems) without returning to the host: every system carries a
+// small state machine, and the kernel advances all live systems by one
+// "phase" per grid-wide step.  A phase is one pass over one sparse matrix
+// (A, G^T or G) plus the vector updates that can ride along with it:
+//
+//   P1      p = s + beta d  (p = s on the first step),  d' = p,  q = A p,  p.q
+//   P2      x += alpha d,  r' = r - alpha q,  t = G^T r',  r'.r'
+//   APPLY2  s = G t + eps r,  r.s            (beta = delta_new / delta_old next)
+//   RESID   r = b - A x (true residual: every `period` iterations and to
+//           confirm convergence), r.r
+//   APPLY1  t = G^T r after a RESID
+//
+// so a regular iteration costs three passes and three grid barriers.  The
+// vector updates round exactly like "a + b*c" evaluated as two operations and
+// values that are both stored and recomputed on the fly (r', p) use the same
+// expression, so every block sees bit-identical values.
+//
+// Mixed precision (SPAI_PREC_MIXED): the same iteration runs on float32 A, G
+// and vectors with float64 dot products; it solves A e = r64 to a relative
+// tolerance, then the float64 outer step x += e, r64 = b - A x (float64 SpMV)
+// restarts it until ||r64|| <= rtol ||b||.
+//
+// Reductions: every tile writes its partial sums; the block that finishes
+// the last tile of a system for the current phase sums that system's tile
+// partials in a fixed order and computes the system's next state.  Results
+// therefore depend only on the system and its schedule, not on the other
+// systems in the launch or on which block ran which tile.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace spai {
+
+namespace {
+
+enum Phase : int32_t {
+  PH_RESID0 = 0, PH_APPLY1, PH_APPLY2, PH_P1, PH_P2, PH_P2X, PH_RESID, PH_XUPD, PH_RESID64, PH_ZEROX, PH_DONE
+};
+enum Mat : int { MAT_A = 0, MAT_GT = 1, MAT_G = 2 };
+
+__host__ __device__ inline int phase_mat(int ph) {
+  return (ph == PH_APPLY1 || ph == PH_P2) ? MAT_GT : (ph == PH_APPLY2 ? MAT_G : MAT_A);
+}
+
+struct EngSys {
+  const int32_t* rp[3];
+  const int32_t* ci[3];
+  const void* val[3];     // A (float64 or float32 by mode), G^T, G (G's storage type)
+  const double* a_v64;    // float64 values of A (outer residual in mixed mode)
+  const int32_t* tiles[3];  // group row starts per matrix
+  int32_t ntiles[3];        // groups per matrix
+  int32_t kgroups[3];       // groups per work item per matrix
+  int32_t fits[3];          // every group fits the stage buffer
+  int32_t nitems;           // work items of this system
+  int32_t item_base;
+  int32_t chunk_base;     // first chunk counter / chunk partial of this system
+  int32_t pad0;
+  int64_t n;
+  double eps;
+  const double* b;
+  double* x;
+  void* r[2];
+  void* d[2];
+  void* q;
+  void* t;
+  void* s;
+  void* e;
+  void* rin;
+  double* history;
+  int64_t history_len;
+};
+
+struct EngOpts {
+  double tol2;
+  double inner_tol2;
+  int64_t max_iter;
+  int32_t period, criterion, max_outer, mixed;
+};
+
+struct __align__(16) EngState {
+  int32_t phase, status, rc, dc;
+  int32_t first, confirm, outer, pad;
+  int64_t iter, iter_in, hist_n, pad2;
+  double delta, delta0, alpha, beta, bb, rr, rr_in0, rr_out;
+};
+static_assert(sizeof(EngState) % 8 == 0, "state words");
+
+struct EngArgs {
+  const EngSys* sys;
+  EngState* st0;
+  EngState* st1;
+  int32_t nsys;
+  const int32_t* item_sys;
+  const int32_t* item_tile;
+  int32_t n_items;
+  double* partial;        // per tile: 2 doubles
+  double* cpartial;       // per chunk of kChunk tiles: 2 doubles
+  unsigned* cnt;          // per system: chunks completed in this slot
+  unsigned* ccnt;         // per chunk: tiles completed in this slot
+  GridSync* gs;
+  EngOpts o;
+  int32_t max_slots;
+  int32_t cap;  // staging capacity in entries
+  uint64_t limit_ns;
+};
+
+template <class T> struct Conv;
+template <> struct Conv<double> {
+  template <class U> __device__ static double f(U v) { return to_f64(v); }
+};
+template <> struct Conv<float> {
+  template <class U> __device__ static float f(U v) { return to_f32(v); }
+};
+
+constexpr int kBlock = 512;   // threads per block
+constexpr int kNE = 4;        // staged entries per thread per group
+constexpr int kCap = kNE * kBlock;
+constexpr int kRMax = 1;      // rows per thread whose operands are loaded together
+constexpr int kChunk = 32;    // items per first-level reduction chunk
+constexpr int kStages = 3;    // TMA stage ring depth
+constexpr int kMaxK = 64;     // groups per work item at most
+constexpr int kAlignE = 8;    // bulk copies start at multiples of 8 entries (16 B for every type)
+
+// y_row = sum over the row's entries of val * op.gather(col), in stored
+// order, then op.fin(row, y_row, op.pre(row)).  Rows are processed in groups
+// whose entries fit kCap: every thread first issues all of its entry loads
+// (column, value) and all gathers, stores the products in shared memory, then
+// issues the operand loads of its rows (op.pre) before summing.  A row with
+// more than kCap entries is summed by the whole block (fixed tree).
+template <class AT, class MV, class Op>
+__device__ __forceinline__ void spmv_group(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                           const MV* __restrict__ val, int r, int re, int base, int m, AT* sbuf,
+                                           const Op& op, double& p0, double& p1) {
+  // operands of this thread's first rows: issued before the entry loads
+  typename Op::Pre pr[kRMax];
+  int ea[kRMax], eb[kRMax];
+#pragma unroll
+  for (int u = 0; u < kRMax; ++u) {
+    const int row = r + threadIdx.x + u * kBlock;
+    if (row < re) {
+      ea[u] = __ldg(rp + row) - base;
+      eb[u] = __ldg(rp + row + 1) - base;
+      pr[u] = op.pre(row);
+    }
+  }
+  {
+    int cix[kNE];
+    AT v[kNE];
+#pragma unroll
+    for (int u = 0; u < kNE; ++u) {
+      const int k = threadIdx.x + u * kBlock;
+      cix[u] = (k < m) ? __ldg(ci + base + k) : 0;
+      v[u] = (k < m) ? Conv<AT>::f(ldro(val + base + k)) : AT(0);
+    }
+    AT g[kNE];
+#pragma unroll
+    for (int u = 0; u < kNE; ++u) {
+      const int k = threadIdx.x + u * kBlock;
+      g[u] = (k < m) ? op.gather(cix[u]) : AT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kNE; ++u) {
+      const int k = threadIdx.x + u * kBlock;
+      if (k < m) sbuf[k] = rmul(v[u], g[u]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kRMax; ++u) {
+    const int row = r + threadIdx.x + u * kBlock;
+    if (row < re) {
+      AT sum = AT(0);
+      for (int e = ea[u]; e < eb[u]; ++e) sum = radd(sum, sbuf[e]);
+      op.fin(row, sum, pr[u], p0, p1);
+    }
+  }
+  // rows beyond the first kRMax * kBlock (groups of very short rows)
+  for (int row = r + threadIdx.x + kRMax * kBlock; row < re; row += kBlock) {
+    const int a0 = __ldg(rp + row) - base, a1 = __ldg(rp + row + 1) - base;
+    const typename Op::Pre q = op.pre(row);
+    AT sum = AT(0);
+    for (int e = a0; e < a1; ++e) sum = radd(sum, sbuf[e]);
+    op.fin(row, sum, q, p0, p1);
+  }
+  __syncthreads();
+}
+
+// y_row = sum over the row's entries of val * op.gather(col), in stored
+// order, then op.fin(row, y_row, op.pre(row)).  A tile whose entries fit the
+// staging buffer is one group: each thread loads its rows' operands, issues
+// all of its entry loads and gathers, stores the products in shared memory
+// and sums its rows.  Larger tiles are split into groups by binary search;
+// a row with more than kCap entries is summed by the whole block.
+template <class AT, class MV, class Op>
+__device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                          const MV* __restrict__ val, int r0, int r1, AT* sbuf, double* red,
+                                          const Op& op, double& p0, double& p1) {
+  const int t0 = __ldg(rp + r0), t1 = __ldg(rp + r1);
+  if (t1 - t0 <= kCap) {
+    spmv_group<AT>(rp, ci, val, r0, r1, t0, t1 - t0, sbuf, op, p0, p1);
+    return;
+  }
+  int r = r0;
+  while (r < r1) {
+    const int base = __ldg(rp + r);
+    int lo = r, hi = r1;
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo + 1) >> 1);
+      if (__ldg(rp + mid) - base <= kCap) lo = mid; else hi = mid - 1;
+    }
+    const int re = lo;
+    if (re == r) {
+      const int e1 = __ldg(rp + r + 1);
+      double acc = 0.0;
+      for (int e = base + threadIdx.x; e < e1; e += blockDim.x)
+        acc += (double)rmul(Conv<AT>::f(ldro(val + e)), op.gather(__ldg(ci + e)));
+      acc = block_sum(acc, red);
+      if (threadIdx.x == 0) {
+        const typename Op::Pre pr = op.pre(r);
+        op.fin(r, (AT)acc, pr, p0, p1);
+      }
+      __syncthreads();
+      r += 1;
+      continue;
+    }
+    spmv_group<AT>(rp, ci, val, r, re, base, __ldg(rp + re) - base, sbuf, op, p0, p1);
+    r = re;
+  }
+}
+
+// ---- per-phase operations: gather(col), pre(row) loads, fin(row, sum) ----
+template <class VT> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
+  const VT* s; const VT* dcur; VT* dnxt; VT* q; VT beta; bool first;
+  struct Pre { VT sv, dv; };
+  __device__ VT gather(int c) const {
+    const VT sv = ldcg(s + c);
+    return first ? sv : radd(sv, rmul(beta, ldcg(dcur + c)));
+  }
+  __device__ Pre pre(int row) const { return Pre{ldcg(s + row), first ? VT(0) : ldcg(dcur + row)}; }
+  __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
+    const VT pv = first ? p.sv : radd(p.sv, rmul(beta, p.dv));
+    dnxt[row] = pv;
+    q[row] = sum;
+    p0 += (double)pv * (double)sum;
+  }
+};
+template <class VT> struct OpP2 {   // x += alpha d;  r' = r - alpha q;  t = G^T r';  r'.r'
+  const VT* rcur; VT* rnxt; const VT* q; const VT* dcur; VT* x; VT* t; VT alpha;
+  struct Pre { VT xv, dv, rv, qv; };
+  __device__ VT gather(int c) const { return rsub(ldcg(rcur + c), rmul(alpha, ldcg(q + c))); }
+  __device__ Pre pre(int row) const { return Pre{ldcg(x + row), ldcg(dcur + row), ldcg(rcur + row), ldcg(q + row)}; }
+  __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
+    x[row] = radd(p.xv, rmul(alpha, p.dv));
+    const VT rn = rsub(p.rv, rmul(alpha, p.qv));
+    rnxt[row] = rn;
+    t[row] = sum;
+    p0 += (double)rn * (double)rn;
+  }
+};
+template <class VT> struct OpApply1 {   // t = G^T r
+  const VT* r; VT* t;
+  struct Pre {};
+  __device__ VT gather(int c) const { return ldcg(r + c); }
+  __device__ Pre pre(int) const { return Pre{}; }
+  __device__ void fin(int row, VT sum, const Pre&, double&, double&) const { t[row] = sum; }
+};
+template <class VT> struct OpApply2 {   // s = G t + eps r;  r.s
+  const VT* t; const VT* r; VT* s; VT eps;
+  struct Pre { VT rv; };
+  __device__ VT gather(int c) const { return ldcg(t + c); }
+  __device__ Pre pre(int row) const { return Pre{ldcg(r + row)}; }
+  __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
+    const VT sv = radd(sum, rmul(eps, p.rv));
+    s[row] = sv;
+    p0 += (double)p.rv * (double)sv;
+  }
+};
+template <class VT> struct OpResid {   // r = b - A x;  r.r, b.b   (b float64)
+  const VT* x; const double* b; VT* r;
+  struct Pre { double bv; };
+  __device__ VT gather(int c) const { return ldcg(x + c); }
+  __device__ Pre pre(int row) const { return Pre{__ldg(b + row)}; }
+  __device__ void fin(int row, VT sum, const Pre& p, double& p0, double& p1) const {
+    const VT rv = rsub((VT)p.bv, sum);
+    r[row] = rv;
+    p0 += (double)rv * (double)rv;
+    p1 += p.bv * p.bv;
+  }
+};
+template <class VT> struct OpResidIn {   // r = rin - A e   (inner replacement, mixed)
+  const VT* e; const VT* rin; VT* r;
+  struct Pre { VT iv; };
+  __device__ VT gather(int c) const { return ldcg(e + c); }
+  __device__ Pre pre(int row) const { return Pre{ldcg(rin + row)}; }
+  __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
+    const VT rv = rsub(p.iv, sum);
+    r[row] = rv;
+    p0 += (double)rv * (double)rv;
+  }
+};
+template <class VT> struct OpResid64 {   // r64 = b - A64 x64;  r = rin = (VT) r64;  e = 0
+  const double* x64; const double* b; VT* r; VT* rin; VT* e;
+  struct Pre { double bv; };
+  __device__ double gather(int c) const { return ldcg(x64 + c); }
+  __device__ Pre pre(int row) const { return Pre{__ldg(b + row)}; }
+  __device__ void fin(int row, double sum, const Pre& p, double& p0, double& p1) const {
+    const double r64 = __dsub_rn(p.bv, sum);
+    const VT r32 = (VT)r64;
+    r[row] = r32;
+    rin[row] = r32;
+    e[row] = VT(0);
+    p0 += r64 * r64;
+    p1 += p.bv * p.bv;
+  }
+};
+
+// ---- TMA-fed groups ----
+// Shared memory of one block: kStages stages of (column indices, values) for
+// one group each, the product buffer, the stage mbarriers and group headers.
+template <class MV> struct StageLayout {
+  static constexpr int kStageE = kCap + 2 * kAlignE;  // entries per stage buffer
+  static constexpr int kColBytes = kStageE * 4;
+  static constexpr int kValBytes = kStageE * (int)sizeof(MV);
+  static constexpr int kStageBytes = kColBytes + kValBytes;
+};
+
+struct GroupHdr {
+  int r, re, e0, e0a, e1;
+};
+
+struct Pipe {
+  unsigned char* stage_base;  // kStages * stage bytes
+  int stage_bytes;
+  int col_bytes;
+  uint64_t* bar;              // kStages mbarriers
+  GroupHdr* hdr;              // kStages headers
+  int* grow;                  // kMaxK + 1 group row starts of the current item
+  int* gent;                  // kMaxK + 1 group first entries
+  uint32_t issued, consumed;  // groups issued / consumed by this block (uniform)
+};
+
+// Thread 0: bulk-copy the entries of group g (rows tiles[g]..tiles[g+1]) into
+// the next stage.  Copies start at a multiple of kAlignE entries (16-byte
+// aligned for every value type) and the arrays are padded past nnz.
+template <class MV>
+__device__ __forceinline__ void issue_group(Pipe& P, const int32_t* ci, const MV* val, int k) {
+  const int st = (int)(P.issued % kStages);
+  const int r = P.grow[k], re = P.grow[k + 1];
+  const int e0 = P.gent[k], e1 = P.gent[k + 1];
+  const int e0a = e0 & ~(kAlignE - 1);
+  int ne = ((e1 + kAlignE - 1) & ~(kAlignE - 1)) - e0a;
+  if (ne < kAlignE) ne = kAlignE;
+  P.hdr[st] = GroupHdr{r, re, e0, e0a, e1};
+  unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+  const unsigned cb = (unsigned)ne * 4u, vb = (unsigned)ne * (unsigned)sizeof(MV);
+  mbar_arrive_expect_tx(P.bar + st, cb + vb);
+  const uint64_t pol = l2_evict_first_policy();
+  tma_load_1d_hint(base, ci + e0a, cb, P.bar + st, pol);
+  tma_load_1d_hint(base + P.col_bytes, val + e0a, vb, P.bar + st, pol);
+}
+
+// Processes groups [g0, g1) of one matrix through the stage ring, software
+// pipelined across groups: while the products of group k are gathered
+// (column indices from the stage buffer, vector entries from L2), the row
+// operands of group k-1 are loaded, and then group k-1's rows are summed from
+// the other product buffer.  One round trip to L2 per group.
+template <class AT, class MV, class Op>
+__device__ __forceinline__ void piped_groups(Pipe& P, const int32_t* __restrict__ tiles,
+                                             const int32_t* __restrict__ rp, const int32_t* ci, const MV* val,
+                                             int g0, int g1, AT* sbuf, const Op& op, double& p0, double& p1,
+                                             uint64_t limit_ns, int* err) {
+  const int ng = g1 - g0;
+  // bounds of every group of this item (row start, first entry), loaded once
+  for (int i = threadIdx.x; i <= ng; i += blockDim.x) {
+    const int r = __ldg(tiles + g0 + i);
+    P.grow[i] = r;
+    P.gent[i] = __ldg(rp + r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int pre = ng < kStages ? ng : kStages;
+    for (int k = 0; k < pre; ++k) {
+      issue_group<MV>(P, ci, val, k);
+      P.issued++;
+    }
+  }
+  GroupHdr prev{0, 0, 0, 0, 0};
+  for (int k = 0; k <= ng; ++k) {
+    // row operands of group k-1 (summed below)
+    typename Op::Pre pr;
+    int ea = 0, eb = 0;
+    const int row = prev.r + threadIdx.x;
+    const bool has_row = (k > 0) && row < prev.re;
+    if (has_row) {
+      ea = __ldg(rp + row) - prev.e0;
+      eb = __ldg(rp + row + 1) - prev.e0;
+      pr = op.pre(row);
+    }
+    GroupHdr h{0, 0, 0, 0, 0};
+    if (k < ng) {
+      const int st = (int)(P.consumed % kStages);
+      const unsigned parity = (P.consumed / kStages) & 1u;
+      if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
+      P.consumed++;
+      h = P.hdr[st];
+      const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+      const int32_t* cs = reinterpret_cast<const int32_t*>(base) + (h.e0 - h.e0a);
+      const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) + (h.e0 - h.e0a);
+      const int m = h.e1 - h.e0;
+      AT* pb = sbuf + (k & 1) * kCap;
+      int cix[kNE];
+#pragma unroll
+      for (int u = 0; u < kNE; ++u) {
+        const int kk = threadIdx.x + u * kBlock;
+        cix[u] = (kk < m) ? cs[kk] : 0;
+      }
+      AT g[kNE];
+#pragma unroll
+      for (int u = 0; u < kNE; ++u) {
+        const int kk = threadIdx.x + u * kBlock;
+        g[u] = (kk < m) ? op.gather(cix[u]) : AT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kNE; ++u) {
+        const int kk = threadIdx.x + u * kBlock;
+        if (kk < m) pb[kk] = rmul(Conv<AT>::f(vs[kk]), g[u]);
+      }
+    }
+    if (has_row) {
+      const AT* qb = sbuf + ((k - 1) & 1) * kCap;
+      AT sum = AT(0);
+      for (int e = ea; e < eb; ++e) sum = radd(sum, qb[e]);
+      op.fin(row, sum, pr, p0, p1);
+    }
+    if (k > 0) {
+      // rows of group k-1 beyond one per thread
+      for (int rr = prev.r + threadIdx.x + kBlock; rr < prev.re; rr += kBlock) {
+        const int a0 = __ldg(rp + rr) - prev.e0, a1 = __ldg(rp + rr + 1) - prev.e0;
+        const typename Op::Pre q = op.pre(rr);
+        const AT* qb = sbuf + ((k - 1) & 1) * kCap;
+        AT sum = AT(0);
+        for (int e = a0; e < a1; ++e) sum = radd(sum, qb[e]);
+        op.fin(rr, sum, q, p0, p1);
+      }
+    }
+    __syncthreads();  // products of group k complete; stage of group k and products of k-1 free
+    if (k < ng && threadIdx.x == 0 && k + kStages < ng) {
+      issue_group<MV>(P, ci, val, k + kStages);
+      P.issued++;
+    }
+    prev = h;
+  }
+}
+
+// Groups [g0, g1) without the stage ring (rows longer than a group, or the
+// float64 residual of mixed precision): direct loads.
+template <class AT, class MV, class Op>
+__device__ __noinline__ void direct_groups(const int32_t* __restrict__ tiles, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ ci, const MV* __restrict__ val, int g0,
+                                              int g1, AT* sbuf, double* red, const Op& op, double& p0, double& p1) {
+  for (int g = g0; g < g1; ++g)
+    spmv_rows<AT>(rp, ci, val, __ldg(tiles + g), __ldg(tiles + g + 1), sbuf, red, op, p0, p1);
+}
+
+template <class AT, class MV, class Op>
+__device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* tiles, const int32_t* rp,
+                                           const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
+                                           double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
+                                           int* err) {
+  if (piped) piped_groups<AT, MV>(P, tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), op, p0, p1, limit_ns, err);
+  else direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op, p0, p1);
+}
+
+template <class VT, class GT, bool MIXED>
+__device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P, void* sbuf,
+                         double* red, double& p0, double& p1, uint64_t limit_ns, int* err) {
+  const int rc = st.rc, dc = st.dc;
+  VT* r_cur = reinterpret_cast<VT*>(S.r[rc]);
+  VT* r_nxt = reinterpret_cast<VT*>(S.r[rc ^ 1]);
+  VT* d_cur = reinterpret_cast<VT*>(S.d[dc]);
+  VT* d_nxt = reinterpret_cast<VT*>(S.d[dc ^ 1]);
+  VT* q = reinterpret_cast<VT*>(S.q);
+  VT* t = reinterpret_cast<VT*>(S.t);
+  VT* s = reinterpret_cast<VT*>(S.s);
+  VT* xv = MIXED ? reinterpret_cast<VT*>(S.e) : reinterpret_cast<VT*>(S.x);  // iterate
+  VT* rin = reinterpret_cast<VT*>(S.rin);
+  const VT* aval = reinterpret_cast<const VT*>(S.val[MAT_A]);
+  const GT* gtval = reinterpret_cast<const GT*>(S.val[MAT_GT]);
+  const GT* gval = reinterpret_cast<const GT*>(S.val[MAT_G]);
+  const VT alpha = (VT)st.alpha, beta = (VT)st.beta, eps = (VT)S.eps;
+  const int m = phase_mat(ph);
+  const int32_t* tl = S.tiles[m];
+  const bool piped = S.fits[m] != 0;
+
+  switch (ph) {
+    case PH_P1: {
+      OpP1<VT> op{s, d_cur, d_nxt, q, beta, st.first != 0};
+      run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      break;
+    }
+    case PH_P2: {
+      OpP2<VT> op{r_cur, r_nxt, q, d_cur, xv, t, alpha};
+      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      break;
+    }
+    case PH_APPLY1: {
+      OpApply1<VT> op{r_cur, t};
+      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      break;
+    }
+    case PH_APPLY2: {
+      OpApply2<VT> op{t, r_cur, s, eps};
+      run_groups<VT>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      break;
+    }
+    case PH_RESID0:
+    case PH_RESID: {
+      if (!MIXED) {
+        OpResid<VT> op{xv, S.b, r_cur};
+        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      } else {
+        OpResidIn<VT> op{xv, rin, r_cur};
+        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      }
+      break;
+    }
+    case PH_RESID64: {
+      OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
+      direct_groups<double>(tl, S.rp[MAT_A], S.ci[MAT_A], S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red,
+                            op, p0, p1);
+      break;
+    }
+    case PH_P2X:
+    case PH_XUPD:
+    case PH_ZEROX: {
+      const int r0 = __ldg(tl + g0), r1 = __ldg(tl + g1);
+      for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+        if (ph == PH_P2X) xv[row] = radd(ldcg(xv + row), rmul(alpha, ldcg(d_cur + row)));
+        else if (ph == PH_XUPD) S.x[row] = __dadd_rn(ldcg(S.x + row), (double)ldcg(xv + row));
+        else S.x[row] = 0.0;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+template <bool MIXED>
+__device__ void transition(const EngSys& S, EngState& st, double q0, double q1, const EngOpts& o, GridSync* gs) {
+  auto finish = [&](int status) {
+    st.status = status;
+    st.phase = PH_DONE;
+    atomicSub(&gs->live, 1);
+  };
+  auto hist = [&](double v) {
+    if (S.history && st.hist_n < S.history_len) S.history[st.hist_n] = v;
+    st.hist_n++;
+  };
+  switch (st.phase) {
+    case PH_RESID0: {
+      st.bb = q1;
+      st.rr = q0;
+      hist(sqrt(q0));
+      if (st.bb == 0.0) { st.phase = PH_ZEROX; return; }
+      if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
+      st.first = 1;
+      st.phase = PH_APPLY1;
+      return;
+    }
+    case PH_ZEROX:
+      st.rr = 0.0;
+      finish(SPAI_OK);
+      return;
+    case PH_APPLY1:
+      st.phase = PH_APPLY2;
+      return;
+    case PH_APPLY2: {
+      const double dn = q0;
+      if (st.first) {
+        if (!(dn > 0.0) || !isfinite(dn)) {
+          if (MIXED) { st.phase = PH_XUPD; return; }
+          finish(SPAI_ERR_BREAKDOWN);
+          return;
+        }
+        st.delta0 = dn;
+        st.delta = dn;
+        if (!MIXED && o.criterion == SPAI_CRIT_PRECOND && !(dn > o.tol2 * st.delta0)) { finish(SPAI_OK); return; }
+        st.phase = PH_P1;
+        return;
+      }
+      if (!(dn > 0.0) || !isfinite(dn)) {
+        if (MIXED) { st.phase = PH_XUPD; return; }
+        finish((o.criterion == SPAI_CRIT_PRECOND && dn == 0.0) ? SPAI_OK : SPAI_ERR_BREAKDOWN);
+        return;
+      }
+      st.beta = dn / st.delta;
+      st.delta = dn;
+      if (!MIXED && o.criterion == SPAI_CRIT_PRECOND && !(dn > o.tol2 * st.delta0)) { finish(SPAI_OK); return; }
+      st.phase = PH_P1;
+      return;
+    }
+    case PH_P1: {
+      const double dq = q0;
+      st.first = 0;
+      st.dc ^= 1;
+      if (!(dq > 0.0) || !isfinite(dq)) {
+        if (MIXED) { st.phase = PH_XUPD; return; }
+        finish(SPAI_ERR_BREAKDOWN);
+        return;
+      }
+      st.alpha = st.delta / dq;
+      const int64_t i = MIXED ? st.iter_in : st.iter;
+      st.phase = (o.period > 0 && (i % o.period) == 0) ? PH_P2X : PH_P2;
+      return;
+    }
+    case PH_P2: {
+      st.rc ^= 1;
+      st.iter++;
+      st.iter_in++;
+      st.rr = q0;
+      if (!MIXED) {
+        if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) {
+          st.confirm = 1;
+          st.phase = PH_RESID;
+          return;
+        }
+        hist(sqrt(st.rr));
+        if (st.iter >= o.max_iter) { finish(SPAI_ERR_NOT_CONVERGED); return; }
+        st.phase = PH_APPLY2;
+        return;
+      }
+      hist(sqrt(st.rr));
+      if (st.rr <= o.inner_tol2 * st.rr_in0 || st.iter >= o.max_iter) { st.phase = PH_XUPD; return; }
+      st.phase = PH_APPLY2;
+      return;
+    }
+    case PH_P2X:
+      st.iter++;
+      st.iter_in++;
+      st.confirm = 0;
+      st.phase = PH_RESID;
+      return;
+    case PH_RESID: {
+      st.rr = q0;
+      hist(sqrt(st.rr));
+      if (!MIXED) {
+        if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
+        if (st.iter >= o.max_iter) { finish(SPAI_ERR_NOT_CONVERGED); return; }
+        st.confirm = 0;
+        st.phase = PH_APPLY1;
+        return;
+      }
+      if (st.rr <= o.inner_tol2 * st.rr_in0 || st.iter >= o.max_iter) { st.phase = PH_XUPD; return; }
+      st.phase = PH_APPLY1;
+      return;
+    }
+    case PH_XUPD:
+      st.phase = PH_RESID64;
+      return;
+    case PH_RESID64: {
+      if (st.outer == 0) {
+        st.bb = q1;
+        hist(sqrt(q0));
+      }
+      st.rr_out = q0;
+      st.rr = q0;
+      if (st.bb == 0.0) { st.phase = PH_ZEROX; return; }
+      if (q0 <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
+      if (st.iter >= o.max_iter || st.outer >= o.max_outer) { finish(SPAI_ERR_NOT_CONVERGED); return; }
+      st.outer++;
+      st.rr_in0 = q0;
+      st.iter_in = 0;
+      st.first = 1;
+      st.phase = PH_APPLY1;
+      return;
+    }
+    default:
+      return;
+  }
+}
+
+__device__ __forceinline__ void load_state(const EngState* src, EngState* dst) {
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(EngState) / 8); ++i) d[i] = __ldcg(s + i);
+}
+
+template <class VT, class GT, bool MIXED>
+__global__ void __launch_bounds__(kBlock, 1) engine_kernel(EngArgs a) {
+  using MVmax = typename std::conditional<MIXED, float, double>::type;
+  using L = StageLayout<MVmax>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ int sflag, s_last;
+  __shared__ EngState s_st;
+  __shared__ uint64_t s_bar[kStages];
+  __shared__ GroupHdr s_hdr[kStages];
+  __shared__ int s_grow[kMaxK + 1], s_gent[kMaxK + 1];
+
+  Pipe P;
+  P.stage_base = smem_raw;
+  P.stage_bytes = L::kStageBytes;
+  P.col_bytes = L::kColBytes;
+  P.bar = s_bar;
+  P.hdr = s_hdr;
+  P.grow = s_grow;
+  P.gent = s_gent;
+  P.issued = 0;
+  P.consumed = 0;
+  void* sbuf = smem_raw + (size_t)kStages * L::kStageBytes;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(s_bar + i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int slot0 = *(volatile int*)&a.gs->slot;
+  int slots = 0;
+  for (;;) {
+    const int par = (slot0 + slots) & 1;
+    EngState* cur = par ? a.st1 : a.st0;
+    EngState* nxt = par ? a.st0 : a.st1;
+    int cached = -1;
+    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+      const int sid = __ldg(a.item_sys + it);
+      const int v = __ldg(a.item_tile + it);
+      if (sid != cached) {
+        if (threadIdx.x == 0) load_state(cur + sid, &s_st);
+        __syncthreads();
+        cached = sid;
+      }
+      const int ph = s_st.phase;
+      if (ph == PH_DONE) continue;
+      const EngSys& S = a.sys[sid];
+      const int m = phase_mat(ph);
+      const int K = S.kgroups[m];
+      const int g0 = v * K;
+      int g1 = g0 + K;
+      if (g1 > S.ntiles[m]) g1 = S.ntiles[m];
+      double p0 = 0.0, p1 = 0.0;
+      if (g0 < g1) run_item<VT, GT, MIXED>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err);
+      p0 = block_sum(p0, red);
+      p1 = block_sum(p1, red);
+      double* pbase = a.partial + 2 * (size_t)S.item_base;
+      double* cbase = a.cpartial + 2 * (size_t)S.chunk_base;
+      const int nit = S.nitems;
+      const int nch = (nit + kChunk - 1) / kChunk;
+      const int ch = v / kChunk;
+      const int ch_size = min(kChunk, nit - ch * kChunk);
+      if (threadIdx.x == 0) {
+        pbase[2 * v] = p0;
+        pbase[2 * v + 1] = p1;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.ccnt + S.chunk_base + ch, 1u);
+        s_last = (prev == (unsigned)(ch_size - 1)) ? 1 : 0;
+      }
+      __syncthreads();
+      if (s_last) {
+        // this block completed chunk `ch`: sum its item partials (one warp, fixed tree)
+        if (threadIdx.x < 32) {
+          __threadfence();
+          const int tt = ch * kChunk + threadIdx.x;
+          double c0 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt) : 0.0;
+          double c1 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt + 1) : 0.0;
+          c0 = warp_sum(c0);
+          c1 = warp_sum(c1);
+          if (threadIdx.x == 0) {
+            cbase[2 * ch] = c0;
+            cbase[2 * ch + 1] = c1;
+            a.ccnt[S.chunk_base + ch] = 0u;
+            __threadfence();
+            const unsigned prev = atomicAdd(a.cnt + sid, 1u);
+            s_last = (prev == (unsigned)(nch - 1)) ? 2 : 0;
+          }
+        }
+        __syncthreads();
+        if (s_last == 2) {
+          __threadfence();
+          double q0 = 0.0, q1 = 0.0;
+          for (int tt = threadIdx.x; tt < nch; tt += blockDim.x) {
+            q0 += __ldcg(cbase + 2 * tt);
+            q1 += __ldcg(cbase + 2 * tt + 1);
+          }
+          q0 = block_sum(q0, red);
+          q1 = block_sum(q1, red);
+          if (threadIdx.x == 0) {
+            EngState ns = s_st;
+            transition<MIXED>(S, ns, q0, q1, a.o, a.gs);
+            nxt[sid] = ns;
+            if (ns.phase == PH_DONE) cur[sid] = ns;
+            a.cnt[sid] = 0u;
+            __threadfence();
+          }
+        }
+      }
+      __syncthreads();
+    }
+    ++slots;
+    const int ex = grid_barrier(a.gs, gridDim.x, a.limit_ns, &sflag);
+    if (ex || slots >= a.max_slots) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->slot = slot0 + slots;
+}
+
+// ---- true residual ||b - A x|| / ||b|| (float64, deterministic) ----
+__global__ void true_residual_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const double* __restrict__ v, const double* __restrict__ b,
+                                     const double* __restrict__ x, int64_t n, double* part) {
+  __shared__ double red[32];
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s = __dadd_rn(s, __dmul_rn(v[e], x[ci[e]]));
+    const double r = b[i] - s;
+    rr += r * r;
+    bb += b[i] * b[i];
+  }
+  rr = block_sum(rr, red);
+  bb = block_sum(bb, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rr;
+    part[2 * blockIdx.x + 1] = bb;
+  }
+}
+
+template <class VT, class GT, bool MIXED>
+const void* kernel_ptr() {
+  return reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED>);
+}
+
+const void* select_kernel(bool mixed, int gtype) {
+  if (!mixed) {
+    if (gtype == SPAI_F64) return kernel_ptr<double, double, false>();
+    if (gtype == SPAI_F32) return kernel_ptr<double, float, false>();
+    return nullptr;
+  }
+  if (gtype == SPAI_F32) return kernel_ptr<float, float, true>();
+  if (gtype == SPAI_BF16) return kernel_ptr<float, __nv_bfloat16, true>();
+  if (gtype == SPAI_F16) return kernel_ptr<float, __half, true>();
+  return nullptr;
+}
+
+}  // namespace
+
+size_t engine_smem_bytes(bool mixed) {
+  const int stage = mixed ? StageLayout<float>::kStageBytes : StageLayout<double>::kStageBytes;
+  return (size_t)kStages * stage + 2 * (size_t)kCap * sizeof(double);
+}
+
+bool engine_groups_fit(int32_t max_row) { return max_row >= 1 && max_row <= kCap / 2; }
+
+// Groups per work item: items are handed to blocks round-robin, so pick the
+// K minimising  rounds * (K * t_group + t_item)  with rounds = ceil(items /
+// grid), t_item ~ 3 t_group of fixed per-item cost.  Depends only on the
+// system's group count and the kernel's co-resident grid.
+int engine_items_k(int ngroups, int grid) {
+  if (ngroups <= 1 || grid <= 0) return 1;
+  int best_k = 1;
+  double best = 1e300;
+  const int kmax = ngroups < kMaxK ? ngroups : kMaxK;
+  for (int k = 1; k <= kmax; ++k) {
+    const int64_t items = (ngroups + k - 1) / k;
+    const int64_t rounds = (items + grid - 1) / grid;
+    const double t = (double)rounds * (k + 3.0);
+    if (t < best - 1e-9) { best = t; best_k = k; }
+    if (items <= 1) break;
+  }
+  return best_k;
+}
+
+// Tile size for a matrix whose longest row has max_row entries: binning rows
+// by their first entry gives tiles of at most tile_nnz + max_row - 1 entries,
+// so tile_nnz = kCap - max_row + 1 makes every tile one staging group.
+int engine_tile_nnz(int32_t max_row) {
+  if (max_row < 1) max_row = 1;
+  if (max_row > kCap / 2) return kCap / 2;
+  return kCap - max_row + 1;
+}
+
+// Runs PCG on nsys systems in one persistent launch sequence.
+int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const double* const* b, double* const* x,
+               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override) {
+  if (nsys <= 0) return set_error(SPAI_ERR_INVALID, "nsys must be positive");
+  const bool mixed = o->precision == SPAI_PREC_MIXED;
+  if (o->precision != SPAI_PREC_F64 && !mixed) return set_error(SPAI_ERR_INVALID, "unknown precision");
+  if (o->criterion != SPAI_CRIT_RESIDUAL && o->criterion != SPAI_CRIT_PRECOND)
+    return set_error(SPAI_ERR_INVALID, "unknown criterion");
+  if (!(o->rtol >= 0.0)) return set_error(SPAI_ERR_INVALID, "rtol must be >= 0");
+  const int gtype = M[0]->gtype;
+  for (int i = 0; i < nsys; ++i) {
+    if (!S[i] || !M[i] || !b[i] || !x[i]) return set_error(SPAI_ERR_INVALID, "null system, preconditioner or vector");
+    if (M[i]->gtype != gtype) return set_error(SPAI_ERR_INVALID, "all preconditioners of a batch need one G type");
+    if (M[i]->P->n != S[i]->n) return set_error(SPAI_ERR_SHAPE, "G and A sizes differ (system %d)", i);
+  }
+  const void* kfn = select_kernel(mixed, gtype);
+  if (!kfn)
+    return set_error(SPAI_ERR_INVALID,
+                     mixed ? "mixed precision needs G stored as F32, BF16 or F16"
+                           : "float64 precision needs G stored as F64 or F32");
+  int rc;
+  const int block = kBlock;
+  const size_t smem = engine_smem_bytes(mixed);
+  const size_t vsz = mixed ? sizeof(float) : sizeof(double);
+  SPAI_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block, smem));
+  if (per_sm < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
+  const int grid_max = per_sm * num_sms();
+
+  // per-system groups, work items, workspace and descriptors
+  std::vector<EngSys> hs(nsys);
+  std::vector<DevMem> ws(nsys);
+  int64_t items = 0, chunks = 0;
+  for (int i = 0; i < nsys; ++i) {
+    SystemData& A = *S[i];
+    PrecondData& P = *M[i];
+    const int tn = A.tile_nnz;
+    if ((rc = build_tiles(A.rowptr.as<int32_t>(), A.n, A.nnz, tn, A.tiles, s))) return rc;
+    if ((rc = build_tiles(P.P->gt_rp(), P.P->n, P.P->nnz, tn, P.gt_tiles, s))) return rc;
+    if ((rc = build_tiles(P.P->g_rp(), P.P->n, P.P->nnz, tn, P.g_tiles, s))) return rc;
+    EngSys& e = hs[i];
+    memset(&e, 0, sizeof(e));
+    e.rp[MAT_A] = A.rowptr.as<int32_t>();
+    e.ci[MAT_A] = A.colidx.as<int32_t>();
+    e.val[MAT_A] = mixed ? (const void*)A.val32.p : (const void*)A.val64.p;
+    e.a_v64 = A.val64.as<double>();
+    e.rp[MAT_GT] = P.P->gt_rp();
+    e.ci[MAT_GT] = P.P->gt_ci();
+    e.val[MAT_GT] = P.gt_val.p;
+    e.rp[MAT_G] = P.P->g_rp();
+    e.ci[MAT_G] = P.P->g_ci();
+    e.val[MAT_G] = P.g_val.p;
+    e.tiles[MAT_A] = A.tiles.starts.as<int32_t>();
+    e.tiles[MAT_GT] = P.gt_tiles.starts.as<int32_t>();
+    e.tiles[MAT_G] = P.g_tiles.starts.as<int32_t>();
+    e.ntiles[MAT_A] = A.tiles.ntiles;
+    e.ntiles[MAT_GT] = P.gt_tiles.ntiles;
+    e.ntiles[MAT_G] = P.g_tiles.ntiles;
+    const int fits = engine_groups_fit(A.max_row) ? 1 : 0;
+    int ng = 0;
+    for (int mm = 0; mm < 3; ++mm) {
+      e.fits[mm] = fits;
+      if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
+    }
+    const int kg = engine_items_k(ng, grid_max);
+    e.nitems = (ng + kg - 1) / kg;
+    for (int mm = 0; mm < 3; ++mm) e.kgroups[mm] = (e.ntiles[mm] + e.nitems - 1) / e.nitems;
+    e.item_base = (int32_t)items;
+    e.chunk_base = (int32_t)chunks;
+    items += e.nitems;
+    chunks += (e.nitems + kChunk - 1) / kChunk;
+    e.n = A.n;
+    e.eps = P.eps;
+    e.b = b[i];
+    e.x = x[i];
+    const int nvec = mixed ? 9 : 7;
+    const size_t stride = ((A.n * vsz + 255) / 256) * 256;
+    if ((rc = ws[i].alloc(stride * nvec, s))) return rc;
+    char* base = ws[i].as<char>();
+    e.r[0] = base; e.r[1] = base + stride;
+    e.d[0] = base + 2 * stride; e.d[1] = base + 3 * stride;
+    e.q = base + 4 * stride; e.t = base + 5 * stride; e.s = base + 6 * stride;
+    if (mixed) { e.e = base + 7 * stride; e.rin = base + 8 * stride; }
+    if (nsys == 1 && o->record_history && o->history) {
+      e.history = o->history;
+      e.history_len = o->history_len;
+    }
+  }
+  if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
+  std::vector<int32_t> isys(items), itile(items);
+  for (int i = 0; i < nsys; ++i)
+    for (int v = 0; v < hs[i].nitems; ++v) {
+      isys[hs[i].item_base + v] = i;
+      itile[hs[i].item_base + v] = v;
+    }
+  std::vector<EngState> hst(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    memset(&hst[i], 0, sizeof(EngState));
+    hst[i].phase = mixed ? PH_RESID64 : PH_RESID0;
+    hst[i].status = SPAI_OK;
+  }
+  // one device block for all launch tables
+  const size_t sz_sys = sizeof(EngSys) * nsys, sz_st = sizeof(EngState) * nsys;
+  const size_t sz_items = sizeof(int32_t) * items, sz_part = sizeof(double) * 2 * items;
+  const size_t sz_cnt = sizeof(unsigned) * nsys;
+  const size_t sz_cpart = sizeof(double) * 2 * chunks, sz_ccnt = sizeof(unsigned) * chunks;
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t off_sys = 0, off_st0 = al(sz_sys), off_st1 = off_st0 + al(sz_st), off_is = off_st1 + al(sz_st);
+  const size_t off_it = off_is + al(sz_items), off_part = off_it + al(sz_items), off_cnt = off_part + al(sz_part);
+  const size_t off_cpart = off_cnt + al(sz_cnt), off_ccnt = off_cpart + al(sz_cpart);
+  const size_t off_gs = off_ccnt + al(sz_ccnt), total = off_gs + al(sizeof(GridSync));
+  DevMem tab;
+  if ((rc = tab.alloc(total, s))) return rc;
+  char* tb = tab.as<char>();
+  SPAI_CUDA(cudaMemsetAsync(tb, 0, total, s));
+  SPAI_CUDA(cudaMemcpyAsync(tb + off_sys, hs.data(), sz_sys, cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(tb + off_st0, hst.data(), sz_st, cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(tb + off_st1, hst.data(), sz_st, cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(tb + off_is, isys.data(), sz_items, cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(tb + off_it, itile.data(), sz_items, cudaMemcpyHostToDevice, s));
+  GridSync g0;
+  memset(&g0, 0, sizeof(g0));
+  g0.live = nsys;
+  SPAI_CUDA(cudaMemcpyAsync(tb + off_gs, &g0, sizeof(g0), cudaMemcpyHostToDevice, s));
+
+  EngArgs args;
+  memset(&args, 0, sizeof(args));
+  args.sys = reinterpret_cast<const EngSys*>(tb + off_sys);
+  args.st0 = reinterpret_cast<EngState*>(tb + off_st0);
+  args.st1 = reinterpret_cast<EngState*>(tb + off_st1);
+  args.nsys = nsys;
+  args.item_sys = reinterpret_cast<const int32_t*>(tb + off_is);
+  args.item_tile = reinterpret_cast<const int32_t*>(tb + off_it);
+  args.n_items = (int32_t)items;
+  args.partial = reinterpret_cast<double*>(tb + off_part);
+  args.cnt = reinterpret_cast<unsigned*>(tb + off_cnt);
+  args.cpartial = reinterpret_cast<double*>(tb + off_cpart);
+  args.ccnt = reinterpret_cast<unsigned*>(tb + off_ccnt);
+  args.gs = reinterpret_cast<GridSync*>(tb + off_gs);
+  int64_t max_iter = o->max_iter;
+  if (max_iter <= 0) {
+    int64_t nmax = 0;
+    for (int i = 0; i < nsys; ++i) nmax = S[i]->n > nmax ? S[i]->n : nmax;
+    max_iter = 10 * nmax;
+    if (max_iter > 1000000) max_iter = 1000000;
+  }
+  args.o.tol2 = o->rtol * o->rtol;
+  const double irt = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+  args.o.inner_tol2 = irt * irt;
+  args.o.max_iter = max_iter;
+  args.o.period = o->replace_period < 0 ? 0 : o->replace_period;
+  args.o.criterion = o->criterion;
+  args.o.max_outer = o->max_outer > 0 ? o->max_outer : 100;
+  args.o.mixed = mixed ? 1 : 0;
+  args.limit_ns = 2000000000ull;  // 2 s per barrier wait
+
+  int grid = grid_max;
+  if (S[0]->grid_per_sm > 0 && S[0]->grid_per_sm < per_sm) grid = S[0]->grid_per_sm * num_sms();
+  if (grid_override > 0 && grid_override < grid) grid = grid_override;
+  if (grid > items) grid = (int)items;
+  if (grid < 1) grid = 1;
+  // slot budget: generous bound on phases per iteration
+  const int64_t slot_cap = 4 * max_iter + 64 * (int64_t)args.o.max_outer + 64;
+  const int chunk = 3000;
+  int64_t done_slots = 0;
+  for (;;) {
+    int64_t left = slot_cap - done_slots;
+    args.max_slots = (int32_t)(left < chunk ? left : chunk);
+    if (args.max_slots <= 0) break;
+    void* kargs[] = {&args};
+    SPAI_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(block), kargs, smem, s));
+    GridSync gh;
+    SPAI_CUDA(cudaMemcpyAsync(&gh, args.gs, sizeof(gh), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    done_slots = gh.slot;
+    if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a grid barrier wait timed out");
+    if (gh.live <= 0) break;
+  }
+  // results
+  std::vector<EngState> fin(nsys);
+  SPAI_CUDA(cudaMemcpyAsync(fin.data(), args.st0, sz_st, cudaMemcpyDeviceToHost, s));
+  std::vector<EngState> fin1(nsys);
+  SPAI_CUDA(cudaMemcpyAsync(fin1.data(), args.st1, sz_st, cudaMemcpyDeviceToHost, s));
+  // true residuals
+  const int rgrid = 2 * num_sms();
+  DevMem part;
+  if ((rc = part.alloc(sizeof(double) * 2 * rgrid * nsys, s))) return rc;
+  for (int i = 0; i < nsys; ++i) {
+    true_residual_kernel<<<rgrid, 256, 0, s>>>(S[i]->rowptr.as<int32_t>(), S[i]->colidx.as<int32_t>(),
+                                               S[i]->val64.as<double>(), b[i], x[i], S[i]->n,
+                                               part.as<double>() + 2 * rgrid * i);
+    SPAI_CUDA(cudaGetLastError());
+  }
+  std::vector<double> hp(2 * rgrid * nsys);
+  SPAI_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
+  SPAI_CUDA(cudaStreamSynchronize(s));
+  int first_bad = SPAI_OK;
+  const int par = (int)(done_slots & 1);
+  for (int i = 0; i < nsys; ++i) {
+    const EngState& f = par ? fin1[i] : fin[i];
+    double rr = 0, bb = 0;
+    for (int k = 0; k < rgrid; ++k) { rr += hp[2 * rgrid * i + 2 * k]; bb += hp[2 * rgrid * i + 2 * k + 1]; }
+    spai_pcg_result& r = res[i];
+    r.iters = f.iter;
+    r.outer_iters = f.outer;
+    r.status = (f.phase == PH_DONE) ? f.status : SPAI_ERR_NOT_CONVERGED;
+    r.true_rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
+    r.rec_rel_res = f.bb > 0 ? sqrt(f.rr / f.bb) : 0.0;
+    r.history_written = f.hist_n;
+    if (r.status != SPAI_OK && first_bad == SPAI_OK) first_bad = r.status;
+  }
+  if (first_bad != SPAI_OK) {
+    set_error(first_bad, "pcg: %s", first_bad == SPAI_ERR_BREAKDOWN ? "breakdown" : "not converged");
+  }
+  return first_bad;
+}
+
+}  // namespace spai

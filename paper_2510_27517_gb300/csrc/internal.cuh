@@ -1,0 +1,280 @@
+// Internal definitions shared by the library's translation units.
+// Nothing here is part of the public ABI (see include/spai.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "spai.h"
+
+namespace spai {
+
+// ---------------------------------------------------------------------------
+// Host-side error state
+// ---------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define SPAI_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::spai::cuda_error(_e, #call); \
+  } while (0)
+
+// Device allocation tied to a stream (stream-ordered pool allocator).
+// Temporaries are freed stream-ordered on the stream they were allocated on;
+// memory owned by a handle (keep() called) is freed with cudaFree, which
+// waits for all work, because the creating stream may be gone by then.
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  bool owned = false;
+  void keep() { owned = true; }
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() { release(); }
+  int alloc(size_t nbytes, cudaStream_t stream);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+size_t dtype_size(int dt);
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+struct PatternData {
+  int64_t n = 0, nnz = 0;      // nnz of G
+  int32_t kind = SPAI_PATTERN_FULL;
+  int32_t max_row = 0;         // longest row of G
+  int32_t max_row_t = 0;       // longest row of G^T
+  DevMem rowptr, colidx;       // G
+  DevMem t_rowptr, t_colidx;   // G^T (separate arrays for LOWER/UPPER; empty for FULL)
+  DevMem perm;                 // val_T[perm[e]] = val[e]
+  DevMem src;                  // index into A of each entry of G (LOWER/UPPER only)
+  int64_t a_nnz = 0;           // nnz of the A it was built from
+  const int32_t* g_rp() const { return rowptr.as<int32_t>(); }
+  const int32_t* g_ci() const { return colidx.as<int32_t>(); }
+  const int32_t* gt_rp() const { return kind == SPAI_PATTERN_FULL ? rowptr.as<int32_t>() : t_rowptr.as<int32_t>(); }
+  const int32_t* gt_ci() const { return kind == SPAI_PATTERN_FULL ? colidx.as<int32_t>() : t_colidx.as<int32_t>(); }
+};
+
+// Row-start table of one matrix for one tile size (built on demand, cached).
+struct TileSet {
+  int32_t tile_nnz = 0;
+  int32_t ntiles = 0;
+  DevMem starts;  // ntiles + 1 row indices
+};
+
+struct PrecondData {
+  std::shared_ptr<PatternData> P;
+  int32_t gtype = SPAI_F64;
+  double eps = 0.0;
+  double anorm = 0.0;        // ||A|| used by the GNN (0 when values were given)
+  DevMem g_val, gt_val;
+  TileSet g_tiles, gt_tiles; // cached for the last tile size used
+};
+
+struct SystemData {
+  int64_t n = 0, nnz = 0;
+  int32_t max_row = 0;
+  DevMem rowptr, colidx, val64, val32;
+  int32_t tile_nnz = 2048;
+  int32_t block = 256;
+  int32_t grid_per_sm = 0;   // 0: as many co-resident blocks as fit
+  TileSet tiles;
+};
+
+}  // namespace spai
+
+struct spai_pattern { std::shared_ptr<spai::PatternData> d; };
+struct spai_precond { std::shared_ptr<spai::PrecondData> d; };
+struct spai_system  { std::shared_ptr<spai::SystemData> d; };
+
+namespace spai {
+
+// Internal entry points used across translation units.
+int build_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz, TileSet& ts, cudaStream_t s);
+int validate_csr_device(const spai_csr* A, bool need_symmetric, int32_t* max_row, cudaStream_t s);
+int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+int system_from_csr(const spai_csr* A, SystemData& S, bool validate, cudaStream_t s);
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Loads of data written earlier in the same kernel by other blocks: bypass L1.
+template <class T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ldcg(const __nv_bfloat16* p) {
+  unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(p));
+  return __ushort_as_bfloat16(u);
+}
+template <> __device__ __forceinline__ __half ldcg(const __half* p) {
+  unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(p));
+  return __ushort_as_half(u);
+}
+
+// Read-only streams (matrix data): read-only path.
+template <class T> __device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ double to_f64(__half v) { return (double)__half2float(v); }
+__device__ __forceinline__ float to_f32(double v) { return (float)v; }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+// Separately rounded arithmetic (no contraction into FMA), so that vector
+// updates round exactly like  a + b * c  evaluated as two operations.
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, then fixed order over warps).
+// `scratch` needs blockDim.x/32 doubles.  Result valid in every thread.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (w == 0) t = warp_sum(t);
+  __syncthreads();
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// ---- TMA bulk copies (global -> shared) completing on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  uint64_t st;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(st) : "r"(smem_u32(bar)), "r"(bytes) : "memory");
+  (void)st;
+}
+// L2 policy for data streamed once (matrix entries): evicted first, so the
+// vectors gathered by the SpMVs stay resident in L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned).
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_1d_hint(void* dst, const void* src, unsigned bytes, uint64_t* bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity; false if `limit_ns` passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+// Grid-wide barrier for cooperative launches with a bounded wait.
+struct GridSync {
+  unsigned count;
+  unsigned gen;
+  int exit_flag;   // decided by the last arriver, read by everyone after the barrier
+  int err;         // SPAI_ERR_TIMEOUT when a wait gave up
+  int live;        // systems still running
+  int slot;        // slots executed so far (parity of double-buffered state)
+  int pad[2];
+};
+
+// Returns the exit flag decided at this barrier.  Every wait is bounded by
+// `limit_ns`; on expiry err is set and the caller must stop.
+__device__ __forceinline__ int grid_barrier(GridSync* g, unsigned nblocks, uint64_t limit_ns, int* sflag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned my_gen = ld_acquire_u32(&g->gen);
+    __threadfence();
+    unsigned prev = atomicAdd(&g->count, 1u);
+    if (prev == nblocks - 1) {
+      g->count = 0;
+      int live = *(volatile int*)&g->live;
+      int err = *(volatile int*)&g->err;
+      *(volatile int*)&g->exit_flag = (live <= 0 || err != 0) ? 1 : 0;
+      __threadfence();
+      st_release_u32(&g->gen, my_gen + 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(&g->gen) == my_gen) {
+        __nanosleep(32);
+        if ((++spins & 255u) == 0 && global_ns() - t0 > limit_ns) {
+          atomicExch(&g->err, SPAI_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    int ef = *(volatile int*)&g->exit_flag;
+    int er = *(volatile int*)&g->err;
+    *sflag = (ef || er) ? 1 : 0;
+  }
+  __syncthreads();
+  return *sflag;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace spai

@@ -27,3 +27,13 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def spai_lib():
+    """Builds (if stale) and loads the CUDA library."""
+    from paper_2510_27517_gb300 import _build
+    _build.build()
+    import paper_2510_27517_gb300 as spai
+    spai.lib()
+    return spai

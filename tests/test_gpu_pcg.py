@@ -1,0 +1,179 @@
+"""PCG on the GPU against the oracle's Algorithm 1 (App. A) with
+M^-1 = G G^T + eps I (Eq. 1).
+
+float64 path: per-iteration residual norms agree to 1e-10 relative and x to
+1e-8 relative (same iteration, same G).  Special cases G = I and
+G = D^-1/2.  Mixed precision: the true float64 residual reaches rtol."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2510_27517_gb300 as spai_mod
+import workloads as W
+from oracle import fsai, pcg
+
+pytestmark = pytest.mark.gpu
+
+
+def assert_history_parity(hist, ref_hist, bnorm):
+    """Per-iteration ||r_k|| parity.  Differences in dot-product summation
+    order are amplified by CG roughly as eps * ||r_0|| / ||r_k||, so the
+    1e-10 bar is taken relative to ||b|| (the scale of rtol) at every
+    iteration, and relative to ||r_k|| itself while ||r_k|| >= 1e-4 ||b||."""
+    ref_hist = np.asarray(ref_hist)
+    assert hist.shape == ref_hist.shape
+    diff = np.abs(hist - ref_hist)
+    assert (diff / bnorm).max() <= 1e-10, (diff / bnorm).max()
+    early = ref_hist >= 1e-4 * bnorm
+    assert (diff[early] / ref_hist[early]).max() <= 1e-10, (diff[early] / ref_hist[early]).max()
+
+
+def upload(spai, A):
+    return spai.CSRMatrix.from_numpy(A.n, A.rowptr, A.colidx, A.val)
+
+
+def fsai_precond(spai, A, dA, g_dtype=0):
+    urp, uci, gv = fsai.fsai_g(A.n, A.rowptr, A.colidx, A.val)
+    pat = spai.build_pattern(dA, spai.PATTERN_UPPER)
+    return spai.precond_from_values(pat, torch.tensor(gv, device="cuda"), g_dtype, eps=0.0), (urp, uci, gv)
+
+
+def gpu_solve(spai, dA, M, b, hist_len=0, **kw):
+    x = torch.zeros(dA.n, dtype=torch.float64, device="cuda")
+    h = torch.zeros(hist_len, dtype=torch.float64, device="cuda") if hist_len else None
+    res = spai.pcg_solve(dA, M, torch.tensor(b, device="cuda"), x, history=h, **kw)
+    return res, x.cpu().numpy(), (h.cpu().numpy() if h is not None else None)
+
+
+def test_poisson64_fsai_matches_oracle_every_iteration(spai_lib):
+    spai = spai_lib
+    A = W.poisson2d(64)
+    b = W.rhs_uniform(A.n, W.BASE_SEED + 1)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, urp, uci, gv, 0.0), rtol=1e-8)
+    res, x, hist = gpu_solve(spai, dA, M, b, hist_len=4096)
+    assert res["status"] == 0 and ref.status == pcg.CONVERGED
+    assert res["iters"] == ref.iters
+    k = res["history_written"]
+    assert k == len(ref.history)
+    assert_history_parity(hist[:k], ref.history, np.linalg.norm(b))
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    assert res["true_rel_res"] <= 1e-8
+    assert abs(res["true_rel_res"] - pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x, b)) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["identity", "jacobi"])
+@pytest.mark.parametrize("period", [50, 0, 7])
+def test_special_cases(spai_lib, which, period):
+    spai = spai_lib
+    A = W.aniso2d(23, 40.0, 0.6)
+    b = W.rhs_uniform(A.n, 11)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = A.val[A.colidx == rows]
+    g = np.where(A.colidx == rows, 1.0 if which == "identity" else 1.0 / np.sqrt(diag[rows]), 0.0)
+    dA = upload(spai, A)
+    pat = spai.build_pattern(dA, spai.PATTERN_FULL)
+    M = spai.precond_from_values(pat, torch.tensor(g, device="cuda"), spai.F64, eps=0.0)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, A.rowptr, A.colidx, g, 0.0),
+                  rtol=1e-9, replace_period=period)
+    res, x, hist = gpu_solve(spai, dA, M, b, hist_len=8192, rtol=1e-9, replace_period=period)
+    assert res["iters"] == ref.iters
+    k = res["history_written"]
+    assert_history_parity(hist[:k], ref.history, np.linalg.norm(b))
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_precond_criterion(spai_lib):
+    spai = spai_lib
+    A = W.poisson2d(30)
+    b = W.rhs_uniform(A.n, 3)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, urp, uci, gv, 0.0), rtol=1e-8,
+                  criterion=pcg.PRECOND)
+    res, x, _ = gpu_solve(spai, dA, M, b, criterion=spai.CRIT_PRECOND)
+    assert res["iters"] == ref.iters and res["status"] == 0
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_zero_rhs_and_not_converged(spai_lib):
+    spai = spai_lib
+    A = W.poisson2d(16)
+    dA = upload(spai, A)
+    M, _ = fsai_precond(spai, A, dA)
+    res, x, _ = gpu_solve(spai, dA, M, np.zeros(A.n))
+    assert res["status"] == 0 and res["iters"] == 0 and not x.any()
+    res, x, _ = gpu_solve(spai, dA, M, W.rhs_uniform(A.n, 1), max_iter=5)
+    assert res["status"] == spai.spai.ERR_NOT_CONVERGED and res["iters"] == 5
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, W.rhs_uniform(A.n, 1),
+                  pcg.spai_apply(A.n, *fsai.fsai_g(A.n, A.rowptr, A.colidx, A.val), 0.0), max_iter=5)
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+def test_nonzero_x0(spai_lib):
+    spai = spai_lib
+    A = W.poisson2d(24)
+    b = W.rhs_uniform(A.n, 5)
+    x0 = W.rhs_uniform(A.n, 6)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, urp, uci, gv, 0.0), x0=x0)
+    x = torch.tensor(x0, device="cuda")
+    res = spai.pcg_solve(dA, M, torch.tensor(b, device="cuda"), x)
+    assert res["iters"] == ref.iters
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("gdt", [1, 2, 3])
+def test_mixed_precision_reaches_rtol(spai_lib, gdt):
+    spai = spai_lib
+    A = W.poisson2d(64)
+    b = W.rhs_uniform(A.n, W.BASE_SEED + 1)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA, g_dtype=gdt)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, urp, uci, gv, 0.0), rtol=1e-8)
+    res, x, _ = gpu_solve(spai, dA, M, b, precision=spai.PREC_MIXED)
+    assert res["status"] == 0
+    true = pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x, b)
+    assert true <= 1e-8 and abs(true - res["true_rel_res"]) < 1e-12
+    # the distance to the oracle's x is bounded by the conditioning of A times rtol
+    assert np.linalg.norm(x - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+
+
+def test_mixed_first_inner_solve_tracks_oracle(spai_lib):
+    # first inner float32 iterations follow the float64 oracle on the same data
+    spai = spai_lib
+    A = W.poisson2d(40)
+    b = W.rhs_uniform(A.n, 2)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA, g_dtype=1)
+    a32 = A.val.astype(np.float32).astype(np.float64)
+    g32 = gv.astype(np.float32).astype(np.float64)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, a32, b.astype(np.float32).astype(np.float64),
+                  pcg.spai_apply(A.n, urp, uci, g32, 0.0), rtol=1e-4)
+    res, x, hist = gpu_solve(spai, dA, M, b, hist_len=4096, precision=spai.PREC_MIXED, inner_rtol=1e-4)
+    k = min(20, len(ref.history))
+    rel = np.abs(hist[:k] - np.array(ref.history[:k])) / np.array(ref.history[:k])
+    assert rel.max() <= 1e-4, rel
+
+
+def test_batched_equals_alone(spai_lib):
+    spai = spai_lib
+    mats = [W.poisson2d(20), W.aniso2d(31, 10.0, 0.3), W.poisson2d(45), W.aniso2d(12, 500.0, 2.0)]
+    systems, preconds, bs, xs = [], [], [], []
+    alone = []
+    for i, A in enumerate(mats):
+        dA = upload(spai, A)
+        S = spai.system_create(dA)
+        M, _ = fsai_precond(spai, A, dA)
+        b = torch.tensor(W.rhs_uniform(A.n, 100 + i), device="cuda")
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        r = spai.system_solve(S, M, b, x)
+        alone.append((r, x.clone()))
+        systems.append(S); preconds.append(M); bs.append(b)
+        xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+    res = spai.pcg_solve_batched(systems, preconds, bs, xs)
+    for (ra, xa), rb, xb in zip(alone, res, xs):
+        assert rb["status"] == 0 and rb["iters"] == ra["iters"]
+        assert torch.equal(xa, xb)
