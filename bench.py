@@ -1,0 +1,445 @@
+"""Benchmark: time to rtol 1e-8 per solve (solves/s) for the SPAI-preconditioned
+CG hot path on one or more GB300s.
+
+A step is one pass of the whole hot path over one system:
+  build_pattern (G on A's pattern + explicit G^T)  ->  GNN forward filling G
+  ->  PCG with M^-1 = G G^T + eps I to ||b - A x|| / ||b|| <= 1e-8
+(float32 inner iterations inside float64 iterative refinement).
+
+Default workload: 3D variable-coefficient diffusion, 7-point finite volumes
+on 128^3 cells (n = 2,097,152, nnz = 14,581,760), log-normal coefficient
+(sigma 1.5, correlation length 8 cells), GNN with seeded random weights
+(L = 4, width 24), b uniform in [-1, 1].
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: launched by torchrun, one rank per GPU; every rank solves its own
+system (independent replicas, no collective on the data path) and rank 0
+prints one JSON line with the aggregate solves/s over the max time of any
+rank.  `--impl reference` times the CPU float64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to rtol 1e-8 (time-to-tolerance per solve)"
+UNIT = "solves/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload_cfg(args):
+    return {"N": args.grid, "sigma": 1.5, "corr_len": 8.0, "eps": args.eps, "layers": 4, "g_dtype": args.gdtype,
+            "precision": "mixed" if args.precision == "mixed" else "f64", "inner_rtol": args.inner_rtol}
+
+
+def make_host_workload(args, rank: int):
+    import numpy as np
+
+    import workloads as W
+
+    A, k = W.diffusion3d(args.grid, 1.5, 8.0, seed=W.BASE_SEED + 2)
+    v = W.diffusion3d_node_features(k)
+    blob = W.gnn_random_weights(4, 4, seed=W.BASE_SEED + 100)
+    b = W.rhs_uniform(A.n, W.BASE_SEED + 10 + rank)
+    return {"A": A, "v": v, "blob": blob, "b": b.astype(np.float64)}
+
+
+def algorithmic_bytes(n, nnz_a, nnz_g, s_v, s_g):
+    """Bytes one inner PCG iteration must move (three passes over A, G^T, G):
+    matrix values and column indices, row pointers, and about 12 vector
+    streams of length n.  The float64 outer step reads A (values + indices)
+    and 4 float64 vectors."""
+    it = (nnz_a * (s_v + 4) + 2 * nnz_g * (s_g + 4) + 3 * (n + 1) * 4 + 12 * n * s_v)
+    outer = nnz_a * 12 + 4 * n * 8
+    return it, outer
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas: no collective on the data path)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(per_rank_ms_total, steps: int, world: int):
+    """Whole-job throughput: every rank did `steps` solves; the job took the
+    longest rank's time."""
+    tmax = max(per_rank_ms_total)
+    return {"value": world * steps / (tmax / 1e3), "ms_per_step": tmax / steps}
+
+
+def barrier_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle baseline (single thread, bounded sample)
+# ---------------------------------------------------------------------------
+def cpu_leg(args):
+    """Times the float64 oracle on a bounded sample of the workload and scales
+    it to one solve: the GNN forward on the first 8 z-slabs of the grid
+    (scaled by stored entries) plus `samp` oracle PCG iterations on the full
+    system (scaled by the iteration count `k`).  Prints one JSON object."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import gnn, pcg
+
+    h = make_host_workload(args, 0)
+    A, v, blob, b = h["A"], h["v"], h["blob"], h["b"]
+    N = args.grid
+    ns = min(A.n, 8 * N * N)
+    m = int(A.rowptr[ns])
+    keep = A.colidx[:m] < ns
+    rows = np.repeat(np.arange(ns), np.diff(A.rowptr[:ns + 1]))
+    sub = W.coo_to_csr(ns, rows[keep], A.colidx[:m][keep], A.val[:m][keep])
+    t0 = time.perf_counter()
+    g_sub = gnn.gnn_forward(sub.n, sub.rowptr, sub.colidx, sub.val, v[:ns], blob)
+    t_gnn_sub = time.perf_counter() - t0
+    t_gnn = t_gnn_sub * A.nnz / sub.nnz
+    # G on the full pattern for the iteration timing: the sub-block's values
+    # tiled (values do not change the cost of an iteration)
+    g = np.resize(g_sub, A.nnz)
+    apply = pcg.spai_apply(A.n, A.rowptr, A.colidx, g, args.eps)
+    samp = args.cpu_iters
+    t0 = time.perf_counter()
+    res = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, apply, rtol=0.0, max_iter=samp, replace_period=50)
+    t_it = (time.perf_counter() - t0) / max(1, res.iters)
+    k = args.cpu_k
+    k_src = "iterations of this run's GPU solve"
+    if k <= 0:
+        # the oracle's own iteration count on the same generator at a 24^3 grid,
+        # scaled by the grid ratio (CG iterations grow like sqrt(cond) ~ 1/h)
+        ns_ = 24
+        As, ks = W.diffusion3d(ns_, 1.5, 8.0, seed=W.BASE_SEED + 2)
+        gs = gnn.gnn_forward(As.n, As.rowptr, As.colidx, As.val, W.diffusion3d_node_features(ks), blob)
+        rs = pcg.pcg(As.n, As.rowptr, As.colidx, As.val, W.rhs_uniform(As.n, W.BASE_SEED + 10),
+                     pcg.spai_apply(As.n, As.rowptr, As.colidx, gs, args.eps), rtol=1e-8)
+        k = int(round(rs.iters * N / ns_))
+        k_src = f"oracle iterations at {ns_}^3 ({rs.iters}) scaled by {N}/{ns_}"
+    t_solve = t_gnn + k * t_it
+    print(json.dumps({"t_gnn_s": t_gnn, "t_iter_s": t_it, "k": k, "k_source": k_src, "t_solve_s": t_solve,
+                      "value": 1.0 / t_solve, "cores": 1,
+                      "sample": f"oracle GNN forward on {ns} of {A.n} rows ({sub.nnz} entries, scaled by nnz) "
+                                f"+ {res.iters} oracle PCG iterations on the full system, scaled to k={k} "
+                                f"({k_src})",
+                      "sample_wall_s": t_gnn_sub + t_it * res.iters}))
+
+
+def run_cpu_leg(args, k: int):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--grid", str(args.grid), "--eps", str(args.eps),
+           "--cpu-k", str(k), "--cpu-iters", str(args.cpu_iters)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2510_27517_gb300 as spai
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spai.lib()
+
+    h = make_host_workload(args, rank)
+    A_h = h["A"]
+    gdt = {"f32": spai.F32, "bf16": spai.BF16, "f16": spai.F16, "f64": spai.F64}[args.gdtype]
+    prec = spai.PREC_MIXED if args.precision == "mixed" else spai.PREC_F64
+    if prec == spai.PREC_F64:
+        gdt = spai.F64
+    A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val, device=dev)
+    v = torch.tensor(h["v"], device=dev)
+    w = torch.tensor(h["blob"], device=dev)
+    b = torch.tensor(h["b"], device=dev)
+    x = torch.zeros(A_h.n, dtype=torch.float64, device=dev)
+    solve_kw = dict(precision=prec, rtol=1e-8, inner_rtol=args.inner_rtol, max_iter=args.max_iter)
+
+    def step():
+        P = spai.build_pattern(A, spai.PATTERN_FULL)
+        M = spai.gnn_precond(A, P, v, w, d_node=4, n_layers=4, g_dtype=gdt, eps=args.eps)
+        x.zero_()
+        r = spai.pcg_solve(A, M, b, x, **solve_kw)
+        M.close()
+        P.close()
+        return r
+
+    results = []
+    for _ in range(args.warmup):
+        results.append(step())
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = spai.kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    timed = []
+    for _ in range(args.steps):
+        timed.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = e0.elapsed_time(e1)
+    launches = spai.kernel_launches() - launches0
+    clk = clocks.stop()
+    for r in timed:
+        if r["status"] != 0 or not (r["true_rel_res"] <= 1e-8):
+            raise RuntimeError(f"solve did not reach rtol 1e-8: {r}")
+    tmax = barrier_max(total_ms, world, dev)
+    agg = aggregate([tmax], args.steps, world)
+
+    # roofline of the persistent PCG kernel (dominant kernel of the step)
+    import workloads  # noqa: F401
+    s_v = 4 if prec == spai.PREC_MIXED else 8
+    s_g = {spai.F64: 8, spai.F32: 4, spai.BF16: 2, spai.F16: 2}[gdt]
+    b_it, b_out = algorithmic_bytes(A_h.n, A_h.nnz, A_h.nnz, s_v, s_g)
+    eng_ms = sum(r["engine_ms"] for r in timed)
+    eng_bytes = sum(r["iters"] * b_it + (r["outer_iters"] + 1) * b_out for r in timed)
+    achieved = eng_bytes / (eng_ms / 1e3) / 1e9
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    traffic = None
+    if args.traffic_per_iter > 0:
+        iters_per_launch = sum(r["iters"] for r in timed) / max(1, sum(r["launches"] for r in timed))
+        traffic = args.traffic_per_iter * iters_per_launch
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+        rp_h, ci_h = pin(A_h.rowptr.astype(np.int32)), pin(A_h.colidx.astype(np.int32))
+        val_h, v_h, b_h = pin(A_h.val), pin(h["v"]), pin(h["b"])
+        w_h = pin(h["blob"])
+        x_h = torch.empty(A_h.n, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in (rp_h, ci_h, val_h, v_h, b_h, w_h))
+        d2h = x_h.numel() * x_h.element_size()
+
+        def e2e_step():
+            A2 = spai.CSRMatrix(A_h.n, rp_h.to(dev, non_blocking=True), ci_h.to(dev, non_blocking=True),
+                                val_h.to(dev, non_blocking=True))
+            v2, w2, b2 = v_h.to(dev, non_blocking=True), w_h.to(dev, non_blocking=True), b_h.to(dev, non_blocking=True)
+            P = spai.build_pattern(A2, spai.PATTERN_FULL)
+            M = spai.gnn_precond(A2, P, v2, w2, d_node=4, n_layers=4, g_dtype=gdt, eps=args.eps)
+            x2 = torch.zeros(A_h.n, dtype=torch.float64, device=dev)
+            r = spai.pcg_solve(A2, M, b2, x2, **solve_kw)
+            x_h.copy_(x2, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            M.close()
+            P.close()
+            return r
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(args.e2e_steps):
+            r = e2e_step()
+            assert r["status"] == 0
+        f1.record()
+        torch.cuda.synchronize()
+        e2e_ms = barrier_max(f0.elapsed_time(f1), world, dev)
+        e2e = {"value": world * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        k = int(round(statistics.mean(r["iters"] for r in timed)))
+        cb = run_cpu_leg(args, k)
+        if "error" not in cb:
+            cpu = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
+                   "t_gnn_s": cb["t_gnn_s"], "t_iter_s": cb["t_iter_s"]}
+        else:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + cb["error"]}
+
+    if rank == 0:
+        r0 = timed[-1]
+        line = {
+            "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": agg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == spai.PREC_MIXED else "f64",
+            "data": "synthetic (seeded generators; random-init GNN weights)",
+            "config": {"workload": f"diffusion3d {args.grid}^3 7-point, GNN-SPAI G ({args.gdtype}), "
+                                   f"{'f32 PCG in f64 refinement' if prec == spai.PREC_MIXED else 'f64 PCG'}",
+                       "n": A_h.n, "nnz": A_h.nnz, "eps": args.eps, "rtol": 1e-8, "inner_rtol": args.inner_rtol,
+                       "gnn_layers": 4, "gnn_width": 24, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (A alone 175 MB > 129 MB)"},
+            "iters": r0["iters"], "outer_iters": r0["outer_iters"], "true_rel_res": r0["true_rel_res"],
+            "engine_ms_per_solve": eng_ms / args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "kernel": "engine_kernel (persistent PCG)",
+                         "peak_source": "measured" if peaks else "fallback",
+                         "bytes_per_iter": b_it},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the float64 CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    last = None
+    for _ in range(args.warmup):
+        run_cpu_leg(args, 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        last = run_cpu_leg(args, 0)
+        if "error" in last:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + last["error"][-200:]}))
+            return
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators; random-init GNN weights)",
+            "config": {"workload": f"diffusion3d {args.grid}^3 7-point, GNN-SPAI G, float64 CPU oracle", "eps": args.eps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": last["cores"],
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "bench_wall_s": wall}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--eps", type=float, default=0.3)
+    ap.add_argument("--gdtype", default="f32", choices=["f32", "bf16", "f16", "f64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--inner-rtol", type=float, default=0.1,
+                    help="mixed: refine x and r in float64 when ||r|| dropped by this factor")
+    ap.add_argument("--max-iter", type=int, default=400000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic-per-iter", type=float, default=0.0,
+                    help="DRAM bytes per inner iteration from an ncu capture of the current kernel")
+    ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-k", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-iters", type=int, default=6, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_leg:
+        cpu_leg(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

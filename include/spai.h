@@ -69,7 +69,7 @@ extern "C" {
 
 /* ----- solver options ----- */
 #define SPAI_PREC_F64   0  /* everything in float64 */
-#define SPAI_PREC_MIXED 1  /* float32 inner PCG inside float64 iterative refinement */
+#define SPAI_PREC_MIXED 1  /* float32 PCG with float64 refinement of x and of the residual */
 
 #define SPAI_CRIT_RESIDUAL 0  /* stop when ||b - A x|| <= rtol ||b|| (tables of Sec. 4.2) */
 #define SPAI_CRIT_PRECOND  1  /* Algorithm 1's own test: r^T M^-1 r <= rtol^2 r0^T M^-1 r0 */
@@ -111,8 +111,11 @@ typedef struct {
   int32_t replace_period;  /* recompute r = b - A x every this many iterations (50); 0 = never */
   int32_t criterion;       /* SPAI_CRIT_* */
   int32_t precision;       /* SPAI_PREC_* */
-  double inner_rtol;       /* mixed only: relative residual reduction per inner solve (<= 0: 1e-4) */
-  int32_t max_outer;       /* mixed only: cap on refinement steps (<= 0: 100) */
+  double inner_rtol;       /* mixed only: when the float32 residual has dropped by this factor since the
+                              last refinement, fold the float32 correction into the float64 x and
+                              replace r by the float64 b - A x (also every replace_period iterations
+                              and to confirm convergence); outside (0, 1): 0.1 */
+  int32_t max_outer;       /* mixed only: cap on float64 refinements (<= 0: none) */
   int32_t record_history;  /* nonzero: write ||r|| after every iteration into `history` */
   double* history;         /* device, history_len doubles (history[0] = ||r_0||), may be NULL */
   int64_t history_len;
@@ -120,11 +123,15 @@ typedef struct {
 
 typedef struct {
   int64_t iters;         /* PCG iterations done (inner iterations for mixed) */
-  int32_t outer_iters;   /* refinement steps (mixed), else 0 */
+  int32_t outer_iters;   /* float64 refinements of x and r (mixed), else 0 */
   int32_t status;        /* SPAI_OK, SPAI_ERR_NOT_CONVERGED, SPAI_ERR_BREAKDOWN, ... */
   double true_rel_res;   /* ||b - A x|| / ||b|| in float64 at exit, computed on the device */
   double rec_rel_res;    /* recurrence residual at exit relative to ||b|| */
   int64_t history_written; /* entries written to opts->history */
+  double engine_ms;      /* device time of the persistent PCG kernel launches (CUDA events on `stream`) */
+  int64_t slots;         /* grid-wide phases the persistent kernel executed */
+  int32_t launches;      /* persistent kernel launches of this solve */
+  int32_t pad;
 } spai_pcg_result;
 
 /* Fills `o` with the defaults (rtol 1e-8, replace_period 50, RESIDUAL, F64). */
@@ -135,6 +142,10 @@ const char* spai_last_error(void);
 
 /* Library version and the CUDA architecture the kernels were built for. */
 const char* spai_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads); lets callers count device work per call. */
+uint64_t spai_kernel_launches(void);
 
 /* ------------------------------------------------------------------------ *
  * build_pattern - sparsity pattern of G and its explicit transpose.
@@ -200,8 +211,10 @@ void spai_system_destroy(spai_system* S);
  * pcg_solve - Algorithm 1 (App. A) with M^-1 = G G^T + eps I (Eq. 1).
  * b and x are device float64 arrays of n entries; x holds x0 on entry and the
  * solution on exit.  With precision MIXED the PCG iterations run in float32
- * (A, G, vectors) with float64 dot products, inside float64 iterative
- * refinement on the true residual.  On SPAI_ERR_NOT_CONVERGED or
+ * (A, G, vectors) with float64 dot products; x is kept in float64 and the
+ * float32 residual is periodically replaced by the float64 true residual
+ * b - A x (iterative refinement without restarting the Krylov recurrence),
+ * so the float64 rtol is reached.  On SPAI_ERR_NOT_CONVERGED or
  * SPAI_ERR_BREAKDOWN x holds the last iterate and `res` is filled.
  * ------------------------------------------------------------------------ */
 int spai_pcg_solve(const spai_csr* A, const spai_precond* M, const double* b, double* x,

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "internal.cuh"
@@ -14,6 +15,9 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
                const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override);
 
 static thread_local std::string g_err = "no error";
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 int set_error(int code, const char* fmt, ...) {
   char buf[1024];
@@ -155,7 +159,7 @@ int make_precond_from_values(const std::shared_ptr<PatternData>& P, const void* 
   M->gt_val.keep();
   if (P->nnz > 0) {
     convert_scatter_kernel<<<grid1(P->nnz), 256, 0, s>>>(g_val, val_dtype, M->g_val.p, M->gt_val.p, g_dtype,
-                                                         P->perm.as<int32_t>(), P->nnz);
+                                                         P->perm.as<int32_t>(), P->nnz); count_launch();
     SPAI_CUDA(cudaGetLastError());
   }
   out = M;
@@ -172,6 +176,8 @@ extern "C" const char* spai_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* spai_version(void) { return "spai-gb300 0.1 (sm_103a)"; }
 
+extern "C" uint64_t spai_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 extern "C" void spai_pcg_opts_default(spai_pcg_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
@@ -180,8 +186,8 @@ extern "C" void spai_pcg_opts_default(spai_pcg_opts* o) {
   o->replace_period = 50;
   o->criterion = SPAI_CRIT_RESIDUAL;
   o->precision = SPAI_PREC_F64;
-  o->inner_rtol = 1e-4;
-  o->max_outer = 100;
+  o->inner_rtol = 0.1;
+  o->max_outer = 0;
 }
 
 extern "C" int spai_precond_from_values(const spai_pattern* P, const void* g_val, int32_t val_dtype, int32_t g_dtype,
@@ -202,8 +208,8 @@ extern "C" int spai_precond_export(const spai_precond* M, void* g_val, void* gt_
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t m = M->d->P->nnz;
   if (m > 0) {
-    if (g_val) export_kernel<<<grid1(m), 256, 0, s>>>(M->d->g_val.p, M->d->gtype, g_val, dtype, m);
-    if (gt_val) export_kernel<<<grid1(m), 256, 0, s>>>(M->d->gt_val.p, M->d->gtype, gt_val, dtype, m);
+    if (g_val) { export_kernel<<<grid1(m), 256, 0, s>>>(M->d->g_val.p, M->d->gtype, g_val, dtype, m); count_launch(); }
+    if (gt_val) { export_kernel<<<grid1(m), 256, 0, s>>>(M->d->gt_val.p, M->d->gtype, gt_val, dtype, m); count_launch(); }
     SPAI_CUDA(cudaGetLastError());
   }
   SPAI_CUDA(cudaStreamSynchronize(s));

@@ -80,16 +80,17 @@ struct EngSys {
 
 struct EngOpts {
   double tol2;
-  double inner_tol2;
+  double reliable2;   // mixed: replace when ||r||^2 <= reliable2 * ||r_ref||^2
   int64_t max_iter;
   int32_t period, criterion, max_outer, mixed;
 };
 
 struct __align__(16) EngState {
   int32_t phase, status, rc, dc;
-  int32_t first, confirm, outer, pad;
-  int64_t iter, iter_in, hist_n, pad2;
-  double delta, delta0, alpha, beta, bb, rr, rr_in0, rr_out;
+  int32_t first, first_resid, outer, e_dirty;
+  int32_t stop, stop_ok, pad0, pad1;
+  int64_t iter, hist_n;
+  double delta, delta0, alpha, beta, bb, rr, rr_ref, pad2;
 };
 static_assert(sizeof(EngState) % 8 == 0, "state words");
 
@@ -544,7 +545,10 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
       const int r0 = __ldg(tl + g0), r1 = __ldg(tl + g1);
       for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
         if (ph == PH_P2X) xv[row] = radd(ldcg(xv + row), rmul(alpha, ldcg(d_cur + row)));
-        else if (ph == PH_XUPD) S.x[row] = __dadd_rn(ldcg(S.x + row), (double)ldcg(xv + row));
+        else if (ph == PH_XUPD) {
+          S.x[row] = __dadd_rn(ldcg(S.x + row), (double)ldcg(xv + row));
+          xv[row] = VT(0);
+        }
         else S.x[row] = 0.0;
       }
       break;
@@ -554,6 +558,16 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   }
 }
 
+// State machine of one system; runs once per phase in the block that
+// completes the system's last work item.  float64 mode follows Algorithm 1
+// with the reading documented in the oracle: the true residual replaces r on
+// iterations i % period == 0 and confirms convergence.  Mixed mode keeps the
+// same iteration in float32 and replaces r by the float64 true residual
+// b - A x (after folding the float32 correction e into the float64 x):
+// every `period` iterations, when ||r|| has dropped by `reliable` since the
+// last replacement, and to confirm convergence.  The Krylov recurrence is not
+// restarted (beta continues from delta_old), so float64 accuracy is reached
+// in about the float64 iteration count.
 template <bool MIXED>
 __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, const EngOpts& o, GridSync* gs) {
   auto finish = [&](int status) {
@@ -565,14 +579,30 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
     if (S.history && st.hist_n < S.history_len) S.history[st.hist_n] = v;
     st.hist_n++;
   };
+  const int RESID_PH = MIXED ? PH_XUPD : PH_RESID;  // how a true residual is obtained
   switch (st.phase) {
-    case PH_RESID0: {
-      st.bb = q1;
+    case PH_RESID0:
+    case PH_RESID64:
+    case PH_RESID: {
+      const bool initial = (st.phase == PH_RESID0) || (MIXED && st.first_resid == 0);
       st.rr = q0;
-      hist(sqrt(q0));
-      if (st.bb == 0.0) { st.phase = PH_ZEROX; return; }
+      if (initial) {
+        st.bb = q1;
+        st.first_resid = 1;
+        hist(sqrt(q0));
+        if (st.bb == 0.0) { st.phase = PH_ZEROX; return; }
+        if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
+        st.rr_ref = st.rr;
+        st.first = 1;
+        st.phase = PH_APPLY1;
+        return;
+      }
+      if (MIXED) st.outer++;
+      hist(sqrt(st.rr));
+      st.rr_ref = st.rr;
       if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
-      st.first = 1;
+      if (st.iter >= o.max_iter || st.stop) { finish(SPAI_ERR_NOT_CONVERGED); return; }
+      if (MIXED && o.max_outer > 0 && st.outer >= o.max_outer) { finish(SPAI_ERR_NOT_CONVERGED); return; }
       st.phase = PH_APPLY1;
       return;
     }
@@ -585,26 +615,21 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
       return;
     case PH_APPLY2: {
       const double dn = q0;
-      if (st.first) {
-        if (!(dn > 0.0) || !isfinite(dn)) {
-          if (MIXED) { st.phase = PH_XUPD; return; }
-          finish(SPAI_ERR_BREAKDOWN);
-          return;
-        }
-        st.delta0 = dn;
-        st.delta = dn;
-        if (!MIXED && o.criterion == SPAI_CRIT_PRECOND && !(dn > o.tol2 * st.delta0)) { finish(SPAI_OK); return; }
-        st.phase = PH_P1;
-        return;
-      }
       if (!(dn > 0.0) || !isfinite(dn)) {
-        if (MIXED) { st.phase = PH_XUPD; return; }
         finish((o.criterion == SPAI_CRIT_PRECOND && dn == 0.0) ? SPAI_OK : SPAI_ERR_BREAKDOWN);
         return;
       }
-      st.beta = dn / st.delta;
+      if (st.first) {
+        st.delta0 = dn;
+      } else {
+        st.beta = dn / st.delta;
+      }
       st.delta = dn;
-      if (!MIXED && o.criterion == SPAI_CRIT_PRECOND && !(dn > o.tol2 * st.delta0)) { finish(SPAI_OK); return; }
+      if (o.criterion == SPAI_CRIT_PRECOND && !(dn > o.tol2 * st.delta0)) {
+        if (MIXED && st.e_dirty) { st.stop_ok = 1; st.phase = PH_XUPD; return; }
+        finish(SPAI_OK);
+        return;
+      }
       st.phase = PH_P1;
       return;
     }
@@ -612,77 +637,43 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
       const double dq = q0;
       st.first = 0;
       st.dc ^= 1;
-      if (!(dq > 0.0) || !isfinite(dq)) {
-        if (MIXED) { st.phase = PH_XUPD; return; }
-        finish(SPAI_ERR_BREAKDOWN);
-        return;
-      }
+      if (!(dq > 0.0) || !isfinite(dq)) { finish(SPAI_ERR_BREAKDOWN); return; }
       st.alpha = st.delta / dq;
-      const int64_t i = MIXED ? st.iter_in : st.iter;
-      st.phase = (o.period > 0 && (i % o.period) == 0) ? PH_P2X : PH_P2;
+      st.phase = (o.period > 0 && (st.iter % o.period) == 0) ? PH_P2X : PH_P2;
       return;
     }
     case PH_P2: {
       st.rc ^= 1;
       st.iter++;
-      st.iter_in++;
+      st.e_dirty = 1;
       st.rr = q0;
-      if (!MIXED) {
-        if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) {
-          st.confirm = 1;
-          st.phase = PH_RESID;
-          return;
-        }
-        hist(sqrt(st.rr));
-        if (st.iter >= o.max_iter) { finish(SPAI_ERR_NOT_CONVERGED); return; }
-        st.phase = PH_APPLY2;
+      if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) {
+        st.phase = RESID_PH;  // confirm with the true residual
+        return;
+      }
+      if (MIXED && st.rr <= o.reliable2 * st.rr_ref) {
+        st.phase = PH_XUPD;  // reliable update
         return;
       }
       hist(sqrt(st.rr));
-      if (st.rr <= o.inner_tol2 * st.rr_in0 || st.iter >= o.max_iter) { st.phase = PH_XUPD; return; }
+      if (st.iter >= o.max_iter) {
+        if (MIXED) { st.stop = 1; st.phase = PH_XUPD; return; }
+        finish(SPAI_ERR_NOT_CONVERGED);
+        return;
+      }
       st.phase = PH_APPLY2;
       return;
     }
     case PH_P2X:
       st.iter++;
-      st.iter_in++;
-      st.confirm = 0;
-      st.phase = PH_RESID;
+      st.e_dirty = 1;
+      st.phase = RESID_PH;
       return;
-    case PH_RESID: {
-      st.rr = q0;
-      hist(sqrt(st.rr));
-      if (!MIXED) {
-        if (o.criterion == SPAI_CRIT_RESIDUAL && st.rr <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
-        if (st.iter >= o.max_iter) { finish(SPAI_ERR_NOT_CONVERGED); return; }
-        st.confirm = 0;
-        st.phase = PH_APPLY1;
-        return;
-      }
-      if (st.rr <= o.inner_tol2 * st.rr_in0 || st.iter >= o.max_iter) { st.phase = PH_XUPD; return; }
-      st.phase = PH_APPLY1;
-      return;
-    }
     case PH_XUPD:
+      st.e_dirty = 0;
+      if (st.stop_ok) { finish(SPAI_OK); return; }
       st.phase = PH_RESID64;
       return;
-    case PH_RESID64: {
-      if (st.outer == 0) {
-        st.bb = q1;
-        hist(sqrt(q0));
-      }
-      st.rr_out = q0;
-      st.rr = q0;
-      if (st.bb == 0.0) { st.phase = PH_ZEROX; return; }
-      if (q0 <= o.tol2 * st.bb) { finish(SPAI_OK); return; }
-      if (st.iter >= o.max_iter || st.outer >= o.max_outer) { finish(SPAI_ERR_NOT_CONVERGED); return; }
-      st.outer++;
-      st.rr_in0 = q0;
-      st.iter_in = 0;
-      st.first = 1;
-      st.phase = PH_APPLY1;
-      return;
-    }
     default:
       return;
   }
@@ -1035,12 +1026,12 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
     if (max_iter > 1000000) max_iter = 1000000;
   }
   args.o.tol2 = o->rtol * o->rtol;
-  const double irt = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
-  args.o.inner_tol2 = irt * irt;
+  const double rel = (o->inner_rtol > 0 && o->inner_rtol < 1) ? o->inner_rtol : 0.1;
+  args.o.reliable2 = rel * rel;
   args.o.max_iter = max_iter;
   args.o.period = o->replace_period < 0 ? 0 : o->replace_period;
   args.o.criterion = o->criterion;
-  args.o.max_outer = o->max_outer > 0 ? o->max_outer : 100;
+  args.o.max_outer = o->max_outer > 0 ? o->max_outer : 0;
   args.o.mixed = mixed ? 1 : 0;
   args.limit_ns = 2000000000ull;  // 2 s per barrier wait
 
@@ -1050,20 +1041,36 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   if (grid > items) grid = (int)items;
   if (grid < 1) grid = 1;
   // slot budget: generous bound on phases per iteration
-  const int64_t slot_cap = 4 * max_iter + 64 * (int64_t)args.o.max_outer + 64;
+  const int64_t slot_cap = 8 * max_iter + 64;
   const int chunk = 3000;
   int64_t done_slots = 0;
+  int launches = 0;
+  double engine_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SPAI_CUDA(cudaEventCreate(&ev0));
+  SPAI_CUDA(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } evg{ev0, ev1};
   for (;;) {
     int64_t left = slot_cap - done_slots;
     args.max_slots = (int32_t)(left < chunk ? left : chunk);
     if (args.max_slots <= 0) break;
     void* kargs[] = {&args};
+    SPAI_CUDA(cudaEventRecord(ev0, s));
     SPAI_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(block), kargs, smem, s));
+    count_launch();
+    SPAI_CUDA(cudaEventRecord(ev1, s));
+    ++launches;
     GridSync gh;
     SPAI_CUDA(cudaMemcpyAsync(&gh, args.gs, sizeof(gh), cudaMemcpyDeviceToHost, s));
     SPAI_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    SPAI_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    engine_ms += ms;
     done_slots = gh.slot;
-    if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a grid barrier wait timed out");
+    if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
     if (gh.live <= 0) break;
   }
   // results
@@ -1078,7 +1085,7 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   for (int i = 0; i < nsys; ++i) {
     true_residual_kernel<<<rgrid, 256, 0, s>>>(S[i]->rowptr.as<int32_t>(), S[i]->colidx.as<int32_t>(),
                                                S[i]->val64.as<double>(), b[i], x[i], S[i]->n,
-                                               part.as<double>() + 2 * rgrid * i);
+                                               part.as<double>() + 2 * rgrid * i); count_launch();
     SPAI_CUDA(cudaGetLastError());
   }
   std::vector<double> hp(2 * rgrid * nsys);
@@ -1097,6 +1104,9 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
     r.true_rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
     r.rec_rel_res = f.bb > 0 ? sqrt(f.rr / f.bb) : 0.0;
     r.history_written = f.hist_n;
+    r.engine_ms = engine_ms;
+    r.slots = done_slots;
+    r.launches = launches;
     if (r.status != SPAI_OK && first_bad == SPAI_OK) first_bad = r.status;
   }
   if (first_bad != SPAI_OK) {

@@ -460,8 +460,8 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   if ((rc = pqm.alloc((size_t)n * 2 * H * sizeof(float), s))) return rc;
   if ((rc = sbuf.alloc((size_t)n * H * sizeof(float), s))) return rc;
 
-  abs_partial_kernel<<<npart, 256, 0, s>>>(static_cast<const double*>(A->val), nnz, part.as<double>());
-  abs_final_kernel<<<1, 256, 0, s>>>(part.as<double>(), npart, nnz, normb.as<double>());
+  abs_partial_kernel<<<npart, 256, 0, s>>>(static_cast<const double*>(A->val), nnz, part.as<double>()); count_launch();
+  abs_final_kernel<<<1, 256, 0, s>>>(part.as<double>(), npart, nnz, normb.as<double>()); count_launch();
   SPAI_CUDA(cudaGetLastError());
 
   // tiles of rows for the edge passes
@@ -482,7 +482,7 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     p.d_node = dn;
     p.has_m = L > 0;
     if (L > 0) split(fm(0), p.m);
-    node_enc_kernel<<<ngrid, nb, 0, s>>>(node_feat, n, xbuf.as<float>(), pqm.as<float>(), p);
+    node_enc_kernel<<<ngrid, nb, 0, s>>>(node_feat, n, xbuf.as<float>(), pqm.as<float>(), p); count_launch();
     SPAI_CUDA(cudaGetLastError());
   }
   EdgeArgs ea;
@@ -522,11 +522,11 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     memcpy(p.W2ee, Ee.W2, sizeof(p.W2ee));
     if (L == 0) {
       fill_decoder(p);
-      edge_kernel<true, true, false, false><<<egrid, ECAP, 0, s>>>(ea, p);
+      edge_kernel<true, true, false, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch();
     } else {
       fill_msg(p, 0);
-      if (raw) edge_kernel<true, false, true, true><<<egrid, ECAP, 0, s>>>(ea, p);
-      else edge_kernel<true, false, true, false><<<egrid, ECAP, 0, s>>>(ea, p);
+      if (raw) { edge_kernel<true, false, true, true><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
+      else { edge_kernel<true, false, true, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
     }
     SPAI_CUDA(cudaGetLastError());
   }
@@ -545,7 +545,7 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     np_.has_m = (t + 1 < L);
     if (np_.has_m) split(fm(t + 1), np_.m);
     node_layer_kernel<<<ngrid, nb, 0, s>>>(P->g_rp(), n, sbuf.as<float>(), xbuf.as<float>(), pqe.as<float>(),
-                                           pqm.as<float>(), np_);
+                                           pqm.as<float>(), np_); count_launch();
     SPAI_CUDA(cudaGetLastError());
     EdgeParams p;
     memset(&p, 0, sizeof(p));
@@ -555,11 +555,11 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     memcpy(p.b2e, e.b2, sizeof(p.b2e));
     if (t + 1 == L) {
       fill_decoder(p);
-      edge_kernel<false, true, false, false><<<egrid, ECAP, 0, s>>>(ea, p);
+      edge_kernel<false, true, false, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch();
     } else {
       fill_msg(p, t + 1);
-      if (raw) edge_kernel<false, false, true, true><<<egrid, ECAP, 0, s>>>(ea, p);
-      else edge_kernel<false, false, true, false><<<egrid, ECAP, 0, s>>>(ea, p);
+      if (raw) { edge_kernel<false, false, true, true><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
+      else { edge_kernel<false, false, true, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
     }
     SPAI_CUDA(cudaGetLastError());
   }

@@ -19,6 +19,7 @@ namespace spai {
 // Host-side error state
 // ---------------------------------------------------------------------------
 int set_error(int code, const char* fmt, ...);
+void count_launch(int n = 1);
 int cuda_error(cudaError_t e, const char* what);
 
 #define SPAI_CUDA(call)                                   \

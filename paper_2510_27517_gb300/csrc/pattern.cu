@@ -180,7 +180,7 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t 
   if (n <= 0) return SPAI_OK;
   const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
   if (nb == 1) {
-    scan_block_kernel<<<1, kScanBlock, 0, s>>>(in, out, nullptr, n);
+    scan_block_kernel<<<1, kScanBlock, 0, s>>>(in, out, nullptr, n); count_launch();
     SPAI_CUDA(cudaGetLastError());
     return SPAI_OK;
   }
@@ -188,10 +188,10 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t 
   int rc;
   if ((rc = sums.alloc(nb * sizeof(int32_t), s))) return rc;
   if ((rc = offs.alloc(nb * sizeof(int32_t), s))) return rc;
-  scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(in, out, sums.as<int32_t>(), n);
+  scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(in, out, sums.as<int32_t>(), n); count_launch();
   SPAI_CUDA(cudaGetLastError());
   if ((rc = exclusive_scan_i32(sums.as<int32_t>(), offs.as<int32_t>(), nb, s))) return rc;
-  scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(out, offs.as<int32_t>(), n);
+  scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(out, offs.as<int32_t>(), n); count_launch();
   SPAI_CUDA(cudaGetLastError());
   return SPAI_OK;
 }
@@ -206,14 +206,14 @@ int validate_csr_device(const spai_csr* A, bool need_symmetric, int32_t* max_row
   if ((rc = fl.alloc(2 * sizeof(int), s))) return rc;
   SPAI_CUDA(cudaMemsetAsync(fl.p, 0, 2 * sizeof(int), s));
   int* flags = fl.as<int>();
-  check_ends_kernel<<<1, 32, 0, s>>>(A->rowptr, A->n, A->nnz, flags);
+  check_ends_kernel<<<1, 32, 0, s>>>(A->rowptr, A->n, A->nnz, flags); count_launch();
   SPAI_CUDA(cudaGetLastError());
   if (A->n > 0) {
     const int block = 256;
     const int64_t warps = A->n;
     int grid = grid_for(warps * 32, block);
     validate_kernel<<<grid, block, 0, s>>>(A->rowptr, A->colidx, A->n, A->nnz, need_symmetric ? 1 : 0, flags,
-                                          flags + 1);
+                                          flags + 1); count_launch();
     SPAI_CUDA(cudaGetLastError());
   }
   int h[2] = {0, 0};
@@ -233,7 +233,7 @@ int build_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz,
   int rc;
   ts.starts.release();
   if ((rc = ts.starts.alloc((nt + 1) * sizeof(int32_t), s))) return rc;
-  tiles_kernel<<<grid_for(nt + 1, 256), 256, 0, s>>>(rowptr, n, nnz, tile_nnz, (int32_t)nt, ts.starts.as<int32_t>());
+  tiles_kernel<<<grid_for(nt + 1, 256), 256, 0, s>>>(rowptr, n, nnz, tile_nnz, (int32_t)nt, ts.starts.as<int32_t>()); count_launch();
   SPAI_CUDA(cudaGetLastError());
   ts.starts.keep();
   ts.ntiles = (int32_t)nt;
@@ -264,7 +264,7 @@ int system_from_csr(const spai_csr* A, SystemData& S, bool validate, cudaStream_
   SPAI_CUDA(cudaMemcpyAsync(S.rowptr.p, A->rowptr, (A->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   SPAI_CUDA(cudaMemcpyAsync(S.colidx.p, A->colidx, A->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   SPAI_CUDA(cudaMemcpyAsync(S.val64.p, A->val, A->nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  f64_to_f32_kernel<<<grid_for(A->nnz, 256), 256, 0, s>>>(S.val64.as<double>(), S.val32.as<float>(), A->nnz);
+  f64_to_f32_kernel<<<grid_for(A->nnz, 256), 256, 0, s>>>(S.val64.as<double>(), S.val32.as<float>(), A->nnz); count_launch();
   SPAI_CUDA(cudaGetLastError());
   S.tiles.starts.release();
   S.tiles.ntiles = 0;
@@ -306,7 +306,7 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
     SPAI_CUDA(cudaMemcpyAsync(P->rowptr.p, A->rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     SPAI_CUDA(cudaMemcpyAsync(P->colidx.p, A->colidx, A->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     perm_kernel<<<grid_for(n, block), block, 0, s>>>(P->g_rp(), P->g_ci(), P->g_rp(), P->g_ci(), n,
-                                                     P->perm.as<int32_t>(), flags.as<int>());
+                                                     P->perm.as<int32_t>(), flags.as<int>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
   } else {
     const int lower_g = (kind == SPAI_PATTERN_LOWER) ? 1 : 0;
@@ -314,12 +314,12 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
     if ((rc = cnt.alloc((n + 1) * sizeof(int32_t), s))) return rc;
     // G
     if ((rc = P->rowptr.alloc((n + 1) * sizeof(int32_t), s))) return rc;
-    count_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, lower_g, cnt.as<int32_t>());
+    count_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, lower_g, cnt.as<int32_t>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     if ((rc = exclusive_scan_i32(cnt.as<int32_t>(), P->rowptr.as<int32_t>(), n + 1, s))) return rc;
     // G^T: the other triangle (the pattern of A is symmetric)
     if ((rc = P->t_rowptr.alloc((n + 1) * sizeof(int32_t), s))) return rc;
-    count_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, 1 - lower_g, cnt.as<int32_t>());
+    count_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, 1 - lower_g, cnt.as<int32_t>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     if ((rc = exclusive_scan_i32(cnt.as<int32_t>(), P->t_rowptr.as<int32_t>(), n + 1, s))) return rc;
     int32_t nnz_g = 0;
@@ -331,14 +331,14 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
     if ((rc = P->src.alloc((nnz_g + 1) * sizeof(int32_t), s))) return rc;
     if ((rc = P->perm.alloc((nnz_g + 1) * sizeof(int32_t), s))) return rc;
     compact_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, lower_g, P->rowptr.as<int32_t>(),
-                                                            P->colidx.as<int32_t>(), P->src.as<int32_t>());
+                                                            P->colidx.as<int32_t>(), P->src.as<int32_t>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     compact_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, 1 - lower_g,
                                                             P->t_rowptr.as<int32_t>(), P->t_colidx.as<int32_t>(),
-                                                            nullptr);
+                                                            nullptr); count_launch();
     SPAI_CUDA(cudaGetLastError());
     perm_kernel<<<grid_for(n, block), block, 0, s>>>(P->g_rp(), P->g_ci(), P->gt_rp(), P->gt_ci(), n,
-                                                     P->perm.as<int32_t>(), flags.as<int>());
+                                                     P->perm.as<int32_t>(), flags.as<int>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     // row lengths bound: a triangle row is no longer than the full row
     P->max_row = P->max_row_t = max_row;

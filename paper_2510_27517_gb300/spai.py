@@ -52,7 +52,8 @@ class _Opts(C.Structure):
 
 class _Res(C.Structure):
     _fields_ = [("iters", C.c_int64), ("outer_iters", C.c_int32), ("status", C.c_int32),
-                ("true_rel_res", C.c_double), ("rec_rel_res", C.c_double), ("history_written", C.c_int64)]
+                ("true_rel_res", C.c_double), ("rec_rel_res", C.c_double), ("history_written", C.c_int64),
+                ("engine_ms", C.c_double), ("slots", C.c_int64), ("launches", C.c_int32), ("pad", C.c_int32)]
 
 
 class _ServeCfg(C.Structure):
@@ -72,6 +73,7 @@ _lib = None
 _SIGS = {
     "spai_last_error": (C.c_char_p, []),
     "spai_version": (C.c_char_p, []),
+    "spai_kernel_launches": (C.c_uint64, []),
     "spai_pcg_opts_default": (None, [C.POINTER(_Opts)]),
     "spai_build_pattern": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_pattern_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -268,7 +270,7 @@ def system_create(A: CSRMatrix, autotune=False, stream=None) -> System:
 
 
 def make_opts(rtol=1e-8, max_iter=0, replace_period=50, criterion=CRIT_RESIDUAL, precision=PREC_F64,
-              inner_rtol=1e-4, max_outer=100, history: torch.Tensor | None = None) -> _Opts:
+              inner_rtol=0.1, max_outer=0, history: torch.Tensor | None = None) -> _Opts:
     o = _Opts()
     lib().spai_pcg_opts_default(C.byref(o))
     o.rtol, o.max_iter, o.replace_period, o.criterion = rtol, max_iter, replace_period, criterion
@@ -281,7 +283,13 @@ def make_opts(rtol=1e-8, max_iter=0, replace_period=50, criterion=CRIT_RESIDUAL,
 
 def _res_dict(r: _Res):
     return {"iters": r.iters, "outer_iters": r.outer_iters, "status": r.status, "true_rel_res": r.true_rel_res,
-            "rec_rel_res": r.rec_rel_res, "history_written": r.history_written}
+            "rec_rel_res": r.rec_rel_res, "history_written": r.history_written, "engine_ms": r.engine_ms,
+            "slots": r.slots, "launches": r.launches}
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by the library so far in this process."""
+    return int(lib().spai_kernel_launches())
 
 
 def _solve_rc(rc):

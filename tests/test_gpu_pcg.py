@@ -177,3 +177,24 @@ def test_batched_equals_alone(spai_lib):
     for (ra, xa), rb, xb in zip(alone, res, xs):
         assert rb["status"] == 0 and rb["iters"] == ra["iters"]
         assert torch.equal(xa, xb)
+
+
+def test_mixed_reliable_updates_track_f64_iteration_count(spai_lib):
+    # float32 iterations with float64 refinement of x and r reach the float64
+    # rtol in about the float64 iteration count (the recurrence is not restarted)
+    spai = spai_lib
+    A = W.aniso2d(90, 300.0, 0.4)
+    b = W.rhs_uniform(A.n, 9)
+    dA = upload(spai, A)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = A.val[A.colidx == rows]
+    g = np.where(A.colidx == rows, 1.0 / np.sqrt(diag[rows]), 0.0)
+    pat = spai.build_pattern(dA, spai.PATTERN_FULL)
+    M64 = spai.precond_from_values(pat, torch.tensor(g, device="cuda"), spai.F64, eps=0.0)
+    M32 = spai.precond_from_values(pat, torch.tensor(g, device="cuda"), spai.F32, eps=0.0)
+    r64, x64, _ = gpu_solve(spai, dA, M64, b)
+    r32, x32, _ = gpu_solve(spai, dA, M32, b, precision=spai.PREC_MIXED)
+    assert r64["status"] == 0 and r32["status"] == 0
+    assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x32, b) <= 1e-8
+    assert r32["iters"] <= 1.3 * r64["iters"] + 10, (r32["iters"], r64["iters"])
+    assert r32["outer_iters"] >= 1
