@@ -239,6 +239,30 @@ int spai_pcg_solve_host(const spai_csr* A, const spai_precond* M, const double* 
                         double* x_host, const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);
 
 /* ------------------------------------------------------------------------ *
+ * pcg_solve_noalloc - float64 PCG that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc while they solve, for example code that runs under
+ * its own device-memory manager or a fixed memory budget where a library
+ * allocation would fail or fragment the pool.  A, G and G^T are raw device
+ * CSRs (float64, the conventions above; G^T must be the explicit transpose
+ * of G, e.g. from spai_pattern_export / spai_precond_export), b and x are
+ * device float64 arrays of n entries (x holds x0 on entry), and
+ * M^-1 = G G^T + eps I.  opts->precision must be SPAI_PREC_F64.
+ * All working memory (vectors, schedules, reductions) lives in one static
+ * device array of 8 MiB that every GPU loading the library holds until the
+ * process exits; it limits n to 131072 rows and each matrix to 4194304
+ * stored entries (larger inputs return SPAI_ERR_TOO_LARGE, and so does any
+ * input whose working set exceeds the array).  The first call on a device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  Every call shares the array and reuses it from the
+ * previous call: calls that overlap on the GPU (other streams or threads)
+ * race, so the caller must serialise them.  res->engine_ms is not measured
+ * (0) since timing events are not created.
+ * ------------------------------------------------------------------------ */
+int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, const spai_csr* GT, double eps, const double* b,
+                           double* x, const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);
+
+/* ------------------------------------------------------------------------ *
  * serve - continuous batching of solve requests on device-resident systems.
  * Requests (b, x on the host) are queued by submit(), which never blocks;
  * a worker thread admits them into free slots while the HBM footprint stays

@@ -33,6 +33,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -1116,3 +1117,257 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
 }
 
 }  // namespace spai
+
+// ---------------------------------------------------------------------------
+// Allocation-free float64 solve.
+//
+// For callers that cannot allocate device memory while they solve (for
+// example code running under a custom device allocator or a memory budget
+// that forbids cudaMalloc), spai_pcg_solve_noalloc takes every matrix as a
+// raw device CSR and keeps all of its working memory in one file-scope
+// device array of kNoAllocBytes.  That array exists on every GPU that loads
+// the library, for the lifetime of the process.  All calls share it: calls
+// that overlap on the GPU (other streams, other host threads) race and must
+// be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace spai {
+
+int launch_validate(const spai_csr* A, int check_sym, int* flags, cudaStream_t s);
+std::string validate_flag_text(int f);
+int launch_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz, int32_t ntiles, int32_t* starts,
+                 cudaStream_t s);
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(8) << 20;   // 8 MiB of device scratch
+constexpr int64_t kNoAllocMaxN = 131072;             // rows at most
+constexpr int64_t kNoAllocMaxNnz = int64_t(1) << 22; // stored entries per matrix at most
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the scratch array, looked up once per device (the
+// symbol's host-side name is not a device address).
+int noalloc_scratch_ptr(unsigned char** out) {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  SPAI_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(SPAI_ERR_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(addr[dev]);
+  return SPAI_OK;
+}
+
+}  // namespace
+
+}  // namespace spai
+
+extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, const spai_csr* GT, double eps,
+                                      const double* b, double* x, const spai_pcg_opts* o, spai_pcg_result* res,
+                                      void* stream) {
+  using namespace spai;
+  if (!A || !G || !GT || !b || !x || !o || !res) return set_error(SPAI_ERR_INVALID, "null argument");
+  if (o->precision != SPAI_PREC_F64)
+    return set_error(SPAI_ERR_INVALID, "the allocation-free solve runs in float64 only (precision F64)");
+  if (o->criterion != SPAI_CRIT_RESIDUAL && o->criterion != SPAI_CRIT_PRECOND)
+    return set_error(SPAI_ERR_INVALID, "unknown criterion");
+  if (!(o->rtol >= 0.0) || !(eps >= 0.0)) return set_error(SPAI_ERR_INVALID, "rtol and eps must be >= 0");
+  const spai_csr* mats[3] = {A, GT, G};
+  for (const spai_csr* m : mats) {
+    if (m->dtype != SPAI_F64) return set_error(SPAI_ERR_INVALID, "A, G and G^T values must be SPAI_F64");
+    if (m->n != A->n) return set_error(SPAI_ERR_SHAPE, "A, G and G^T must have the same n");
+    if (m->n <= 0 || m->n > kNoAllocMaxN || m->nnz < 0 || m->nnz > kNoAllocMaxNnz)
+      return set_error(SPAI_ERR_TOO_LARGE, "allocation-free solve supports n in 1..%lld and nnz <= %lld per matrix",
+                       (long long)kNoAllocMaxN, (long long)kNoAllocMaxNnz);
+  }
+  if (G->nnz != GT->nnz) return set_error(SPAI_ERR_SHAPE, "G and G^T must have the same nnz");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  int rc;
+  if ((rc = noalloc_scratch_ptr(&base))) return rc;
+  const int64_t n = A->n;
+
+  // kernel and grid
+  const void* kfn = select_kernel(false, SPAI_F64);
+  const int block = kBlock;
+  const size_t smem = engine_smem_bytes(false);
+  SPAI_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block, smem));
+  if (per_sm < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
+  const int grid_max = per_sm * num_sms();
+
+  // scratch layout: [flags 3x2 ints | tiles A, G^T, G | tables | partials | vectors]
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  size_t off = 0;
+  const size_t off_flags = off; off += al(6 * sizeof(int));
+  SPAI_CUDA(cudaMemsetAsync(base + off_flags, 0, 6 * sizeof(int), s));
+  for (int k = 0; k < 3; ++k)
+    if ((rc = launch_validate(mats[k], 0, reinterpret_cast<int*>(base + off_flags) + 2 * k, s))) return rc;
+  int hf[6];
+  SPAI_CUDA(cudaMemcpyAsync(hf, base + off_flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+  SPAI_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 3; ++k)
+    if (hf[2 * k]) return set_error(SPAI_ERR_BAD_CSR, "invalid CSR (%s): %s", k == 0 ? "A" : (k == 1 ? "G^T" : "G"),
+                                    validate_flag_text(hf[2 * k]).c_str());
+  int32_t max_row = hf[1];
+  if (hf[3] > max_row) max_row = hf[3];
+  if (hf[5] > max_row) max_row = hf[5];
+  const int32_t tn = engine_tile_nnz(max_row);
+  int32_t ntl[3];
+  size_t off_tiles[3];
+  for (int k = 0; k < 3; ++k) {
+    int64_t nt = (mats[k]->nnz + tn - 1) / tn;
+    if (nt < 1) nt = 1;
+    ntl[k] = (int32_t)nt;
+    off_tiles[k] = off;
+    off += al((nt + 1) * sizeof(int32_t));
+  }
+  EngSys e;
+  memset(&e, 0, sizeof(e));
+  for (int k = 0; k < 3; ++k) {
+    e.rp[k] = mats[k]->rowptr;
+    e.ci[k] = mats[k]->colidx;
+    e.val[k] = mats[k]->val;
+    e.tiles[k] = reinterpret_cast<const int32_t*>(base + off_tiles[k]);
+    e.ntiles[k] = ntl[k];
+    e.fits[k] = 0;  // caller arrays carry no alignment padding: direct loads
+  }
+  e.a_v64 = static_cast<const double*>(A->val);
+  int ng = ntl[0] > ntl[1] ? ntl[0] : ntl[1];
+  if (ntl[2] > ng) ng = ntl[2];
+  const int kg = engine_items_k(ng, grid_max);
+  e.nitems = (ng + kg - 1) / kg;
+  for (int k = 0; k < 3; ++k) e.kgroups[k] = (ntl[k] + e.nitems - 1) / e.nitems;
+  e.item_base = 0;
+  e.chunk_base = 0;
+  e.n = n;
+  e.eps = eps;
+  e.b = b;
+  e.x = x;
+  if (o->record_history && o->history) {
+    e.history = o->history;
+    e.history_len = o->history_len;
+  }
+  const int items = e.nitems, chunks = (e.nitems + kChunk - 1) / kChunk;
+  const size_t off_sys = off; off += al(sizeof(EngSys));
+  const size_t off_st0 = off; off += al(sizeof(EngState));
+  const size_t off_st1 = off; off += al(sizeof(EngState));
+  const size_t off_is = off; off += al(sizeof(int32_t) * items);
+  const size_t off_it = off; off += al(sizeof(int32_t) * items);
+  const size_t off_zero = off;  // everything from here to off_vec starts at zero
+  const size_t off_part = off; off += al(sizeof(double) * 2 * items);
+  const size_t off_cpart = off; off += al(sizeof(double) * 2 * chunks);
+  const size_t off_cnt = off; off += al(sizeof(unsigned));
+  const size_t off_ccnt = off; off += al(sizeof(unsigned) * chunks);
+  const size_t off_gs = off; off += al(sizeof(GridSync));
+  const int rgrid = 2 * num_sms();
+  const size_t off_rpart = off; off += al(sizeof(double) * 2 * rgrid);
+  const size_t off_vec = off;
+  const size_t stride = al(n * sizeof(double));
+  off += 7 * stride;
+  if (off > kNoAllocBytes)
+    return set_error(SPAI_ERR_TOO_LARGE, "allocation-free solve needs %zu bytes of scratch, %zu available", off,
+                     kNoAllocBytes);
+  unsigned char* vb = base + off_vec;
+  e.r[0] = vb; e.r[1] = vb + stride;
+  e.d[0] = vb + 2 * stride; e.d[1] = vb + 3 * stride;
+  e.q = vb + 4 * stride; e.t = vb + 5 * stride; e.s = vb + 6 * stride;
+
+  for (int k = 0; k < 3; ++k)
+    if ((rc = launch_tiles(mats[k]->rowptr, n, mats[k]->nnz, tn, ntl[k],
+                           reinterpret_cast<int32_t*>(base + off_tiles[k]), s)))
+      return rc;
+  EngState st;
+  memset(&st, 0, sizeof(st));
+  st.phase = PH_RESID0;
+  st.status = SPAI_OK;
+  std::vector<int32_t> isys(items, 0), itile(items);
+  for (int v = 0; v < items; ++v) itile[v] = v;
+  GridSync g0;
+  memset(&g0, 0, sizeof(g0));
+  g0.live = 1;
+  SPAI_CUDA(cudaMemsetAsync(base + off_zero, 0, off_vec - off_zero, s));
+  SPAI_CUDA(cudaMemcpyAsync(base + off_sys, &e, sizeof(e), cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(base + off_st0, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(base + off_st1, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(base + off_is, isys.data(), sizeof(int32_t) * items, cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(base + off_it, itile.data(), sizeof(int32_t) * items, cudaMemcpyHostToDevice, s));
+  SPAI_CUDA(cudaMemcpyAsync(base + off_gs, &g0, sizeof(g0), cudaMemcpyHostToDevice, s));
+
+  EngArgs args;
+  memset(&args, 0, sizeof(args));
+  args.sys = reinterpret_cast<const EngSys*>(base + off_sys);
+  args.st0 = reinterpret_cast<EngState*>(base + off_st0);
+  args.st1 = reinterpret_cast<EngState*>(base + off_st1);
+  args.nsys = 1;
+  args.item_sys = reinterpret_cast<const int32_t*>(base + off_is);
+  args.item_tile = reinterpret_cast<const int32_t*>(base + off_it);
+  args.n_items = items;
+  args.partial = reinterpret_cast<double*>(base + off_part);
+  args.cpartial = reinterpret_cast<double*>(base + off_cpart);
+  args.cnt = reinterpret_cast<unsigned*>(base + off_cnt);
+  args.ccnt = reinterpret_cast<unsigned*>(base + off_ccnt);
+  args.gs = reinterpret_cast<GridSync*>(base + off_gs);
+  int64_t max_iter = o->max_iter;
+  if (max_iter <= 0) max_iter = (10 * n < 1000000) ? 10 * n : 1000000;
+  args.o.tol2 = o->rtol * o->rtol;
+  args.o.reliable2 = 0.01;
+  args.o.max_iter = max_iter;
+  args.o.period = o->replace_period < 0 ? 0 : o->replace_period;
+  args.o.criterion = o->criterion;
+  args.o.max_outer = 0;
+  args.o.mixed = 0;
+  args.limit_ns = 2000000000ull;
+  int grid = grid_max < items ? grid_max : items;
+  if (grid < 1) grid = 1;
+  const int64_t slot_cap = 8 * max_iter + 64;
+  const int chunk = 3000;
+  int64_t done_slots = 0;
+  int launches = 0;
+  for (;;) {
+    const int64_t left = slot_cap - done_slots;
+    args.max_slots = (int32_t)(left < chunk ? left : chunk);
+    if (args.max_slots <= 0) break;
+    void* kargs[] = {&args};
+    SPAI_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(block), kargs, smem, s));
+    count_launch();
+    ++launches;
+    GridSync gh;
+    SPAI_CUDA(cudaMemcpyAsync(&gh, args.gs, sizeof(gh), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    done_slots = gh.slot;
+    if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
+    if (gh.live <= 0) break;
+  }
+  EngState fin;
+  SPAI_CUDA(cudaMemcpyAsync(&fin, (done_slots & 1) ? args.st1 : args.st0, sizeof(fin), cudaMemcpyDeviceToHost, s));
+  double* rpart = reinterpret_cast<double*>(base + off_rpart);
+  true_residual_kernel<<<rgrid, 256, 0, s>>>(A->rowptr, A->colidx, static_cast<const double*>(A->val), b, x, n, rpart);
+  count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  std::vector<double> hp(2 * rgrid);
+  SPAI_CUDA(cudaMemcpyAsync(hp.data(), rpart, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
+  SPAI_CUDA(cudaStreamSynchronize(s));
+  double rr = 0, bb = 0;
+  for (int k = 0; k < rgrid; ++k) { rr += hp[2 * k]; bb += hp[2 * k + 1]; }
+  memset(res, 0, sizeof(*res));
+  res->iters = fin.iter;
+  res->outer_iters = 0;
+  res->status = (fin.phase == PH_DONE) ? fin.status : SPAI_ERR_NOT_CONVERGED;
+  res->true_rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
+  res->rec_rel_res = fin.bb > 0 ? sqrt(fin.rr / fin.bb) : 0.0;
+  res->history_written = fin.hist_n;
+  res->engine_ms = 0.0;
+  res->slots = done_slots;
+  res->launches = launches;
+  if (res->status != SPAI_OK)
+    set_error(res->status, "pcg: %s", res->status == SPAI_ERR_BREAKDOWN ? "breakdown" : "not converged");
+  return res->status;
+}

@@ -176,6 +176,28 @@ std::string flag_text(int f) {
 
 }  // namespace
 
+// Launchers over caller-provided memory (no allocation): CSR validation into
+// flags[0] (defect bits) and flags[1] (longest row), and the tile table.
+int launch_validate(const spai_csr* A, int check_sym, int* flags, cudaStream_t s) {
+  check_ends_kernel<<<1, 32, 0, s>>>(A->rowptr, A->n, A->nnz, flags); count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  if (A->n > 0) {
+    validate_kernel<<<grid_for(A->n * 32, 256), 256, 0, s>>>(A->rowptr, A->colidx, A->n, A->nnz, check_sym, flags,
+                                                             flags + 1); count_launch();
+    SPAI_CUDA(cudaGetLastError());
+  }
+  return SPAI_OK;
+}
+
+std::string validate_flag_text(int f) { return flag_text(f); }
+
+int launch_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz, int32_t ntiles, int32_t* starts,
+                 cudaStream_t s) {
+  tiles_kernel<<<grid_for(ntiles + 1, 256), 256, 0, s>>>(rowptr, n, nnz, tile_nnz, ntiles, starts); count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  return SPAI_OK;
+}
+
 int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return SPAI_OK;
   const int64_t nb = (n + kScanBlock - 1) / kScanBlock;

@@ -98,6 +98,8 @@ _SIGS = {
                                          C.POINTER(_Res), C.c_void_p]),
     "spai_pcg_solve_host": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts),
                                       C.POINTER(_Res), C.c_void_p]),
+    "spai_pcg_solve_noalloc": (C.c_int, [C.POINTER(_CSR), C.POINTER(_CSR), C.POINTER(_CSR), C.c_double, C.c_void_p,
+                                         C.c_void_p, C.POINTER(_Opts), C.POINTER(_Res), C.c_void_p]),
     "spai_server_create": (C.c_int, [C.POINTER(_ServeCfg), C.POINTER(C.c_void_p)]),
     "spai_server_register": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
     "spai_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)]),
@@ -330,6 +332,20 @@ def pcg_solve_host(A: CSRMatrix, M: Precond, b_host, x_host, stream=None, **kw):
     r = _Res()
     _solve_rc(lib().spai_pcg_solve_host(C.byref(A._c()), M.h, C.c_void_p(b_host.data_ptr()),
                                         C.c_void_p(x_host.data_ptr()), C.byref(o), C.byref(r), _stream(stream)))
+    return _res_dict(r)
+
+
+def pcg_solve_noalloc(A: CSRMatrix, G: CSRMatrix, GT: CSRMatrix, eps: float, b: torch.Tensor, x: torch.Tensor,
+                      stream=None, **kw):
+    """float64 PCG that allocates no device memory (spai_pcg_solve_noalloc):
+    G and GT are device CSRs of G and its explicit transpose; all working
+    memory comes from the library's static device scratch array."""
+    assert b.dtype == torch.float64 and x.dtype == torch.float64 and b.is_cuda and x.is_cuda
+    o = make_opts(**kw)
+    r = _Res()
+    a_c, g_c, gt_c = A._c(), G._c(), GT._c()
+    _solve_rc(lib().spai_pcg_solve_noalloc(C.byref(a_c), C.byref(g_c), C.byref(gt_c), float(eps), _ptr(b), _ptr(x),
+                                           C.byref(o), C.byref(r), _stream(stream)))
     return _res_dict(r)
 
 
