@@ -879,209 +879,245 @@ int engine_tile_nnz(int32_t max_row) {
   return kCap - max_row + 1;
 }
 
-// Runs PCG on nsys systems in one persistent launch sequence.
-int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const double* const* b, double* const* x,
-               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override) {
-  if (nsys <= 0) return set_error(SPAI_ERR_INVALID, "nsys must be positive");
-  const bool mixed = o->precision == SPAI_PREC_MIXED;
-  if (o->precision != SPAI_PREC_F64 && !mixed) return set_error(SPAI_ERR_INVALID, "unknown precision");
-  if (o->criterion != SPAI_CRIT_RESIDUAL && o->criterion != SPAI_CRIT_PRECOND)
-    return set_error(SPAI_ERR_INVALID, "unknown criterion");
-  if (!(o->rtol >= 0.0)) return set_error(SPAI_ERR_INVALID, "rtol must be >= 0");
-  const int gtype = M[0]->gtype;
-  for (int i = 0; i < nsys; ++i) {
-    if (!S[i] || !M[i] || !b[i] || !x[i]) return set_error(SPAI_ERR_INVALID, "null system, preconditioner or vector");
-    if (M[i]->gtype != gtype) return set_error(SPAI_ERR_INVALID, "all preconditioners of a batch need one G type");
-    if (M[i]->P->n != S[i]->n) return set_error(SPAI_ERR_SHAPE, "G and A sizes differ (system %d)", i);
-  }
-  const void* kfn = select_kernel(mixed, gtype);
-  if (!kfn)
-    return set_error(SPAI_ERR_INVALID,
-                     mixed ? "mixed precision needs G stored as F32, BF16 or F16"
-                           : "float64 precision needs G stored as F64 or F32");
-  int rc;
-  const int block = kBlock;
-  const size_t smem = engine_smem_bytes(mixed);
+size_t engine_work_bytes(int64_t n, bool mixed) {
   const size_t vsz = mixed ? sizeof(float) : sizeof(double);
-  SPAI_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block, smem));
-  if (per_sm < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
-  const int grid_max = per_sm * num_sms();
+  const size_t stride = ((n * vsz + 255) / 256) * 256;
+  return stride * (mixed ? 9 : 7) + 256;
+}
 
-  // per-system groups, work items, workspace and descriptors
-  std::vector<EngSys> hs(nsys);
-  std::vector<DevMem> ws(nsys);
-  int64_t items = 0, chunks = 0;
-  for (int i = 0; i < nsys; ++i) {
-    SystemData& A = *S[i];
-    PrecondData& P = *M[i];
-    const int tn = A.tile_nnz;
-    if ((rc = build_tiles(A.rowptr.as<int32_t>(), A.n, A.nnz, tn, A.tiles, s))) return rc;
-    if ((rc = build_tiles(P.P->gt_rp(), P.P->n, P.P->nnz, tn, P.gt_tiles, s))) return rc;
-    if ((rc = build_tiles(P.P->g_rp(), P.P->n, P.P->nnz, tn, P.g_tiles, s))) return rc;
-    EngSys& e = hs[i];
-    memset(&e, 0, sizeof(e));
-    e.rp[MAT_A] = A.rowptr.as<int32_t>();
-    e.ci[MAT_A] = A.colidx.as<int32_t>();
-    e.val[MAT_A] = mixed ? (const void*)A.val32.p : (const void*)A.val64.p;
-    e.a_v64 = A.val64.as<double>();
-    e.rp[MAT_GT] = P.P->gt_rp();
-    e.ci[MAT_GT] = P.P->gt_ci();
-    e.val[MAT_GT] = P.gt_val.p;
-    e.rp[MAT_G] = P.P->g_rp();
-    e.ci[MAT_G] = P.P->g_ci();
-    e.val[MAT_G] = P.g_val.p;
-    e.tiles[MAT_A] = A.tiles.starts.as<int32_t>();
-    e.tiles[MAT_GT] = P.gt_tiles.starts.as<int32_t>();
-    e.tiles[MAT_G] = P.g_tiles.starts.as<int32_t>();
-    e.ntiles[MAT_A] = A.tiles.ntiles;
-    e.ntiles[MAT_GT] = P.gt_tiles.ntiles;
-    e.ntiles[MAT_G] = P.g_tiles.ntiles;
-    const int fits = engine_groups_fit(A.max_row) ? 1 : 0;
-    int ng = 0;
-    for (int mm = 0; mm < 3; ++mm) {
-      e.fits[mm] = fits;
-      if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
-    }
-    const int kg = engine_items_k(ng, grid_max);
-    e.nitems = (ng + kg - 1) / kg;
-    for (int mm = 0; mm < 3; ++mm) e.kgroups[mm] = (e.ntiles[mm] + e.nitems - 1) / e.nitems;
-    e.item_base = (int32_t)items;
-    e.chunk_base = (int32_t)chunks;
-    items += e.nitems;
-    chunks += (e.nitems + kChunk - 1) / kChunk;
-    e.n = A.n;
-    e.eps = P.eps;
-    e.b = b[i];
-    e.x = x[i];
-    const int nvec = mixed ? 9 : 7;
-    const size_t stride = ((A.n * vsz + 255) / 256) * 256;
-    if ((rc = ws[i].alloc(stride * nvec, s))) return rc;
-    char* base = ws[i].as<char>();
-    e.r[0] = base; e.r[1] = base + stride;
-    e.d[0] = base + 2 * stride; e.d[1] = base + 3 * stride;
-    e.q = base + 4 * stride; e.t = base + 5 * stride; e.s = base + 6 * stride;
-    if (mixed) { e.e = base + 7 * stride; e.rin = base + 8 * stride; }
-    if (nsys == 1 && o->record_history && o->history) {
-      e.history = o->history;
-      e.history_len = o->history_len;
-    }
-  }
-  if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
-  std::vector<int32_t> isys(items), itile(items);
-  for (int i = 0; i < nsys; ++i)
-    for (int v = 0; v < hs[i].nitems; ++v) {
-      isys[hs[i].item_base + v] = i;
-      itile[hs[i].item_base + v] = v;
-    }
-  std::vector<EngState> hst(nsys);
-  for (int i = 0; i < nsys; ++i) {
-    memset(&hst[i], 0, sizeof(EngState));
-    hst[i].phase = mixed ? PH_RESID64 : PH_RESID0;
-    hst[i].status = SPAI_OK;
-  }
-  // one device block for all launch tables
-  const size_t sz_sys = sizeof(EngSys) * nsys, sz_st = sizeof(EngState) * nsys;
-  const size_t sz_items = sizeof(int32_t) * items, sz_part = sizeof(double) * 2 * items;
-  const size_t sz_cnt = sizeof(unsigned) * nsys;
-  const size_t sz_cpart = sizeof(double) * 2 * chunks, sz_ccnt = sizeof(unsigned) * chunks;
-  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
-  const size_t off_sys = 0, off_st0 = al(sz_sys), off_st1 = off_st0 + al(sz_st), off_is = off_st1 + al(sz_st);
-  const size_t off_it = off_is + al(sz_items), off_part = off_it + al(sz_items), off_cnt = off_part + al(sz_part);
-  const size_t off_cpart = off_cnt + al(sz_cnt), off_ccnt = off_cpart + al(sz_cpart);
-  const size_t off_gs = off_ccnt + al(sz_ccnt), total = off_gs + al(sizeof(GridSync));
-  DevMem tab;
-  if ((rc = tab.alloc(total, s))) return rc;
-  char* tb = tab.as<char>();
-  SPAI_CUDA(cudaMemsetAsync(tb, 0, total, s));
-  SPAI_CUDA(cudaMemcpyAsync(tb + off_sys, hs.data(), sz_sys, cudaMemcpyHostToDevice, s));
-  SPAI_CUDA(cudaMemcpyAsync(tb + off_st0, hst.data(), sz_st, cudaMemcpyHostToDevice, s));
-  SPAI_CUDA(cudaMemcpyAsync(tb + off_st1, hst.data(), sz_st, cudaMemcpyHostToDevice, s));
-  SPAI_CUDA(cudaMemcpyAsync(tb + off_is, isys.data(), sz_items, cudaMemcpyHostToDevice, s));
-  SPAI_CUDA(cudaMemcpyAsync(tb + off_it, itile.data(), sz_items, cudaMemcpyHostToDevice, s));
-  GridSync g0;
-  memset(&g0, 0, sizeof(g0));
-  g0.live = nsys;
-  SPAI_CUDA(cudaMemcpyAsync(tb + off_gs, &g0, sizeof(g0), cudaMemcpyHostToDevice, s));
+// A set of systems advanced together by the persistent kernel.  Members keep
+// their own state across launches; the set can be replaced between launches
+// (the server admits and retires systems that way).
+class EngineBatch {
+ public:
+  struct Member {
+    SystemData* S;
+    PrecondData* M;
+    const double* b;
+    double* x;
+    void* work;              // engine_work_bytes(n, mixed) bytes of device memory
+    double* history;
+    int64_t history_len;
+    EngState st;             // state to start from (fresh or carried over)
+  };
 
-  EngArgs args;
-  memset(&args, 0, sizeof(args));
-  args.sys = reinterpret_cast<const EngSys*>(tb + off_sys);
-  args.st0 = reinterpret_cast<EngState*>(tb + off_st0);
-  args.st1 = reinterpret_cast<EngState*>(tb + off_st1);
-  args.nsys = nsys;
-  args.item_sys = reinterpret_cast<const int32_t*>(tb + off_is);
-  args.item_tile = reinterpret_cast<const int32_t*>(tb + off_it);
-  args.n_items = (int32_t)items;
-  args.partial = reinterpret_cast<double*>(tb + off_part);
-  args.cnt = reinterpret_cast<unsigned*>(tb + off_cnt);
-  args.cpartial = reinterpret_cast<double*>(tb + off_cpart);
-  args.ccnt = reinterpret_cast<unsigned*>(tb + off_ccnt);
-  args.gs = reinterpret_cast<GridSync*>(tb + off_gs);
-  int64_t max_iter = o->max_iter;
-  if (max_iter <= 0) {
-    int64_t nmax = 0;
-    for (int i = 0; i < nsys; ++i) nmax = S[i]->n > nmax ? S[i]->n : nmax;
-    max_iter = 10 * nmax;
-    if (max_iter > 1000000) max_iter = 1000000;
+  static EngState fresh_state(bool mixed) {
+    EngState st;
+    memset(&st, 0, sizeof(st));
+    st.phase = mixed ? PH_RESID64 : PH_RESID0;
+    st.status = SPAI_OK;
+    return st;
   }
-  args.o.tol2 = o->rtol * o->rtol;
-  const double rel = (o->inner_rtol > 0 && o->inner_rtol < 1) ? o->inner_rtol : 0.1;
-  args.o.reliable2 = rel * rel;
-  args.o.max_iter = max_iter;
-  args.o.period = o->replace_period < 0 ? 0 : o->replace_period;
-  args.o.criterion = o->criterion;
-  args.o.max_outer = o->max_outer > 0 ? o->max_outer : 0;
-  args.o.mixed = mixed ? 1 : 0;
-  args.limit_ns = 2000000000ull;  // 2 s per barrier wait
 
-  int grid = grid_max;
-  if (S[0]->grid_per_sm > 0 && S[0]->grid_per_sm < per_sm) grid = S[0]->grid_per_sm * num_sms();
-  if (grid_override > 0 && grid_override < grid) grid = grid_override;
-  if (grid > items) grid = (int)items;
-  if (grid < 1) grid = 1;
-  // slot budget: generous bound on phases per iteration
-  const int64_t slot_cap = 8 * max_iter + 64;
-  const int chunk = 3000;
-  int64_t done_slots = 0;
-  int launches = 0;
-  double engine_ms = 0.0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  SPAI_CUDA(cudaEventCreate(&ev0));
-  SPAI_CUDA(cudaEventCreate(&ev1));
-  struct EvGuard {
-    cudaEvent_t a, b;
-    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
-  } evg{ev0, ev1};
-  for (;;) {
-    int64_t left = slot_cap - done_slots;
-    args.max_slots = (int32_t)(left < chunk ? left : chunk);
-    if (args.max_slots <= 0) break;
-    void* kargs[] = {&args};
-    SPAI_CUDA(cudaEventRecord(ev0, s));
-    SPAI_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(block), kargs, smem, s));
+  int init(bool mixed, int gtype, const spai_pcg_opts& o, cudaStream_t s) {
+    mixed_ = mixed;
+    s_ = s;
+    opts_ = o;
+    kfn_ = select_kernel(mixed, gtype);
+    if (!kfn_)
+      return set_error(SPAI_ERR_INVALID, mixed ? "mixed precision needs G stored as F32, BF16 or F16"
+                                               : "float64 precision needs G stored as F64 or F32");
+    smem_ = engine_smem_bytes(mixed);
+    SPAI_CUDA(cudaFuncSetAttribute(kfn_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_));
+    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_, kfn_, kBlock, smem_));
+    if (per_sm_ < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
+    grid_max_ = per_sm_ * num_sms();
+    return SPAI_OK;
+  }
+
+  int grid_max() const { return grid_max_; }
+
+  // Builds the launch tables for `members` (a member whose state is DONE
+  // takes no work).  grid_override > 0 caps the grid.
+  int set_members(const std::vector<Member>& members, int grid_override = 0) {
+    int rc;
+    const int nsys = (int)members.size();
+    nsys_ = nsys;
+    std::vector<EngSys> hs(nsys);
+    int64_t items = 0, chunks = 0, nmax = 0;
+    int live = 0;
+    for (int i = 0; i < nsys; ++i) {
+      const Member& mb = members[i];
+      SystemData& A = *mb.S;
+      PrecondData& P = *mb.M;
+      const int tn = A.tile_nnz;
+      if ((rc = build_tiles(A.rowptr.as<int32_t>(), A.n, A.nnz, tn, A.tiles, s_))) return rc;
+      if ((rc = build_tiles(P.P->gt_rp(), P.P->n, P.P->nnz, tn, P.gt_tiles, s_))) return rc;
+      if ((rc = build_tiles(P.P->g_rp(), P.P->n, P.P->nnz, tn, P.g_tiles, s_))) return rc;
+      EngSys& e = hs[i];
+      memset(&e, 0, sizeof(e));
+      e.rp[MAT_A] = A.rowptr.as<int32_t>();
+      e.ci[MAT_A] = A.colidx.as<int32_t>();
+      e.val[MAT_A] = mixed_ ? (const void*)A.val32.p : (const void*)A.val64.p;
+      e.a_v64 = A.val64.as<double>();
+      e.rp[MAT_GT] = P.P->gt_rp();
+      e.ci[MAT_GT] = P.P->gt_ci();
+      e.val[MAT_GT] = P.gt_val.p;
+      e.rp[MAT_G] = P.P->g_rp();
+      e.ci[MAT_G] = P.P->g_ci();
+      e.val[MAT_G] = P.g_val.p;
+      e.tiles[MAT_A] = A.tiles.starts.as<int32_t>();
+      e.tiles[MAT_GT] = P.gt_tiles.starts.as<int32_t>();
+      e.tiles[MAT_G] = P.g_tiles.starts.as<int32_t>();
+      e.ntiles[MAT_A] = A.tiles.ntiles;
+      e.ntiles[MAT_GT] = P.gt_tiles.ntiles;
+      e.ntiles[MAT_G] = P.g_tiles.ntiles;
+      const int fits = engine_groups_fit(A.max_row) ? 1 : 0;
+      int ng = 0;
+      for (int mm = 0; mm < 3; ++mm) {
+        e.fits[mm] = fits;
+        if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
+      }
+      // work items depend only on the system and the kernel's full grid, so a
+      // system's reductions are identical alone and in any batch
+      const int kg = engine_items_k(ng, grid_max_);
+      e.nitems = (ng + kg - 1) / kg;
+      for (int mm = 0; mm < 3; ++mm) e.kgroups[mm] = (e.ntiles[mm] + e.nitems - 1) / e.nitems;
+      e.item_base = (int32_t)items;
+      e.chunk_base = (int32_t)chunks;
+      items += e.nitems;
+      chunks += (e.nitems + kChunk - 1) / kChunk;
+      e.n = A.n;
+      e.eps = P.eps;
+      e.b = mb.b;
+      e.x = mb.x;
+      const size_t vsz = mixed_ ? sizeof(float) : sizeof(double);
+      const size_t stride = ((A.n * vsz + 255) / 256) * 256;
+      char* base = static_cast<char*>(mb.work);
+      e.r[0] = base; e.r[1] = base + stride;
+      e.d[0] = base + 2 * stride; e.d[1] = base + 3 * stride;
+      e.q = base + 4 * stride; e.t = base + 5 * stride; e.s = base + 6 * stride;
+      if (mixed_) { e.e = base + 7 * stride; e.rin = base + 8 * stride; }
+      e.history = mb.history;
+      e.history_len = mb.history_len;
+      if (A.n > nmax) nmax = A.n;
+      if (mb.st.phase != PH_DONE) ++live;
+    }
+    if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
+    std::vector<int32_t> isys(items), itile(items);
+    for (int i = 0; i < nsys; ++i)
+      for (int v = 0; v < hs[i].nitems; ++v) {
+        isys[hs[i].item_base + v] = i;
+        itile[hs[i].item_base + v] = v;
+      }
+    std::vector<EngState> hst(nsys);
+    for (int i = 0; i < nsys; ++i) hst[i] = members[i].st;
+    const size_t sz_sys = sizeof(EngSys) * nsys, sz_st = sizeof(EngState) * nsys;
+    const size_t sz_items = sizeof(int32_t) * items, sz_part = sizeof(double) * 2 * items;
+    const size_t sz_cnt = sizeof(unsigned) * nsys;
+    const size_t sz_cpart = sizeof(double) * 2 * chunks, sz_ccnt = sizeof(unsigned) * chunks;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t off_sys = 0, off_st0 = al(sz_sys), off_st1 = off_st0 + al(sz_st), off_is = off_st1 + al(sz_st);
+    const size_t off_it = off_is + al(sz_items), off_part = off_it + al(sz_items), off_cnt = off_part + al(sz_part);
+    const size_t off_cpart = off_cnt + al(sz_cnt), off_ccnt = off_cpart + al(sz_cpart);
+    const size_t off_gs = off_ccnt + al(sz_ccnt), total = off_gs + al(sizeof(GridSync));
+    if ((rc = tab_.alloc(total, s_))) return rc;
+    char* tb = tab_.as<char>();
+    SPAI_CUDA(cudaMemsetAsync(tb, 0, total, s_));
+    SPAI_CUDA(cudaMemcpyAsync(tb + off_sys, hs.data(), sz_sys, cudaMemcpyHostToDevice, s_));
+    SPAI_CUDA(cudaMemcpyAsync(tb + off_st0, hst.data(), sz_st, cudaMemcpyHostToDevice, s_));
+    SPAI_CUDA(cudaMemcpyAsync(tb + off_st1, hst.data(), sz_st, cudaMemcpyHostToDevice, s_));
+    SPAI_CUDA(cudaMemcpyAsync(tb + off_is, isys.data(), sz_items, cudaMemcpyHostToDevice, s_));
+    SPAI_CUDA(cudaMemcpyAsync(tb + off_it, itile.data(), sz_items, cudaMemcpyHostToDevice, s_));
+    GridSync g0;
+    memset(&g0, 0, sizeof(g0));
+    g0.live = live;
+    SPAI_CUDA(cudaMemcpyAsync(tb + off_gs, &g0, sizeof(g0), cudaMemcpyHostToDevice, s_));
+    // host copies must stay alive until the copies ran
+    SPAI_CUDA(cudaStreamSynchronize(s_));
+    live_ = live;
+
+    memset(&args_, 0, sizeof(args_));
+    args_.sys = reinterpret_cast<const EngSys*>(tb + off_sys);
+    args_.st0 = reinterpret_cast<EngState*>(tb + off_st0);
+    args_.st1 = reinterpret_cast<EngState*>(tb + off_st1);
+    args_.nsys = nsys;
+    args_.item_sys = reinterpret_cast<const int32_t*>(tb + off_is);
+    args_.item_tile = reinterpret_cast<const int32_t*>(tb + off_it);
+    args_.n_items = (int32_t)items;
+    args_.partial = reinterpret_cast<double*>(tb + off_part);
+    args_.cnt = reinterpret_cast<unsigned*>(tb + off_cnt);
+    args_.cpartial = reinterpret_cast<double*>(tb + off_cpart);
+    args_.ccnt = reinterpret_cast<unsigned*>(tb + off_ccnt);
+    args_.gs = reinterpret_cast<GridSync*>(tb + off_gs);
+    int64_t max_iter = opts_.max_iter;
+    if (max_iter <= 0) {
+      max_iter = 10 * nmax;
+      if (max_iter > 1000000) max_iter = 1000000;
+    }
+    max_iter_ = max_iter;
+    args_.o.tol2 = opts_.rtol * opts_.rtol;
+    const double rel = (opts_.inner_rtol > 0 && opts_.inner_rtol < 1) ? opts_.inner_rtol : 0.1;
+    args_.o.reliable2 = rel * rel;
+    args_.o.max_iter = max_iter;
+    args_.o.period = opts_.replace_period < 0 ? 0 : opts_.replace_period;
+    args_.o.criterion = opts_.criterion;
+    args_.o.max_outer = opts_.max_outer > 0 ? opts_.max_outer : 0;
+    args_.o.mixed = mixed_ ? 1 : 0;
+    args_.limit_ns = 2000000000ull;  // 2 s per device-side wait
+    grid_ = grid_max_;
+    if (grid_override > 0 && grid_override < grid_) grid_ = grid_override;
+    if (grid_ > items) grid_ = (int)items;
+    if (grid_ < 1) grid_ = 1;
+    slots_ = 0;
+    return SPAI_OK;
+  }
+
+  int64_t max_iter() const { return max_iter_; }
+  int live() const { return live_; }
+  int64_t slots() const { return slots_; }
+
+  // One persistent launch of at most max_slots phases; *ms = its device time
+  // when events are given.
+  int launch(int max_slots, cudaEvent_t ev0, cudaEvent_t ev1, double* ms) {
+    if (live_ <= 0) return SPAI_OK;
+    args_.max_slots = max_slots;
+    void* kargs[] = {&args_};
+    if (ev0) SPAI_CUDA(cudaEventRecord(ev0, s_));
+    SPAI_CUDA(cudaLaunchCooperativeKernel(kfn_, dim3(grid_), dim3(kBlock), kargs, smem_, s_));
     count_launch();
-    SPAI_CUDA(cudaEventRecord(ev1, s));
-    ++launches;
+    if (ev1) SPAI_CUDA(cudaEventRecord(ev1, s_));
     GridSync gh;
-    SPAI_CUDA(cudaMemcpyAsync(&gh, args.gs, sizeof(gh), cudaMemcpyDeviceToHost, s));
-    SPAI_CUDA(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    SPAI_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-    engine_ms += ms;
-    done_slots = gh.slot;
+    SPAI_CUDA(cudaMemcpyAsync(&gh, args_.gs, sizeof(gh), cudaMemcpyDeviceToHost, s_));
+    SPAI_CUDA(cudaStreamSynchronize(s_));
+    if (ev0 && ev1 && ms) {
+      float f = 0.f;
+      SPAI_CUDA(cudaEventElapsedTime(&f, ev0, ev1));
+      *ms += f;
+    }
+    slots_ = gh.slot;
+    live_ = gh.live;
     if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
-    if (gh.live <= 0) break;
+    return SPAI_OK;
   }
-  // results
-  std::vector<EngState> fin(nsys);
-  SPAI_CUDA(cudaMemcpyAsync(fin.data(), args.st0, sz_st, cudaMemcpyDeviceToHost, s));
-  std::vector<EngState> fin1(nsys);
-  SPAI_CUDA(cudaMemcpyAsync(fin1.data(), args.st1, sz_st, cudaMemcpyDeviceToHost, s));
-  // true residuals
+
+  // Current state of every member.
+  int read_states(std::vector<EngState>& out) {
+    out.resize(nsys_);
+    SPAI_CUDA(cudaMemcpyAsync(out.data(), (slots_ & 1) ? args_.st1 : args_.st0, sizeof(EngState) * nsys_,
+                              cudaMemcpyDeviceToHost, s_));
+    SPAI_CUDA(cudaStreamSynchronize(s_));
+    return SPAI_OK;
+  }
+
+ private:
+  bool mixed_ = false;
+  cudaStream_t s_ = nullptr;
+  spai_pcg_opts opts_;
+  const void* kfn_ = nullptr;
+  size_t smem_ = 0;
+  int per_sm_ = 0, grid_max_ = 0, grid_ = 0, nsys_ = 0, live_ = 0;
+  int64_t max_iter_ = 0, slots_ = 0;
+  DevMem tab_;
+  EngArgs args_;
+};
+
+// ||b - A x|| / ||b|| for each system (float64, deterministic).
+int engine_true_residuals(int nsys, SystemData* const* S, const double* const* b, double* const* x, double* out,
+                          cudaStream_t s) {
   const int rgrid = 2 * num_sms();
   DevMem part;
+  int rc;
   if ((rc = part.alloc(sizeof(double) * 2 * rgrid * nsys, s))) return rc;
   for (int i = 0; i < nsys; ++i) {
     true_residual_kernel<<<rgrid, 256, 0, s>>>(S[i]->rowptr.as<int32_t>(), S[i]->colidx.as<int32_t>(),
@@ -1092,29 +1128,179 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   std::vector<double> hp(2 * rgrid * nsys);
   SPAI_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
   SPAI_CUDA(cudaStreamSynchronize(s));
-  int first_bad = SPAI_OK;
-  const int par = (int)(done_slots & 1);
   for (int i = 0; i < nsys; ++i) {
-    const EngState& f = par ? fin1[i] : fin[i];
     double rr = 0, bb = 0;
     for (int k = 0; k < rgrid; ++k) { rr += hp[2 * rgrid * i + 2 * k]; bb += hp[2 * rgrid * i + 2 * k + 1]; }
-    spai_pcg_result& r = res[i];
-    r.iters = f.iter;
-    r.outer_iters = f.outer;
-    r.status = (f.phase == PH_DONE) ? f.status : SPAI_ERR_NOT_CONVERGED;
-    r.true_rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
-    r.rec_rel_res = f.bb > 0 ? sqrt(f.rr / f.bb) : 0.0;
-    r.history_written = f.hist_n;
-    r.engine_ms = engine_ms;
-    r.slots = done_slots;
-    r.launches = launches;
-    if (r.status != SPAI_OK && first_bad == SPAI_OK) first_bad = r.status;
+    out[i] = bb > 0 ? sqrt(rr / bb) : 0.0;
   }
-  if (first_bad != SPAI_OK) {
+  return SPAI_OK;
+}
+
+int engine_check_opts(const spai_pcg_opts* o) {
+  if (o->precision != SPAI_PREC_F64 && o->precision != SPAI_PREC_MIXED)
+    return set_error(SPAI_ERR_INVALID, "unknown precision");
+  if (o->criterion != SPAI_CRIT_RESIDUAL && o->criterion != SPAI_CRIT_PRECOND)
+    return set_error(SPAI_ERR_INVALID, "unknown criterion");
+  if (!(o->rtol >= 0.0)) return set_error(SPAI_ERR_INVALID, "rtol must be >= 0");
+  return SPAI_OK;
+}
+
+void engine_fill_result(const EngState& f, double true_rel, double engine_ms, int64_t slots, int launches,
+                        spai_pcg_result& r) {
+  memset(&r, 0, sizeof(r));
+  r.iters = f.iter;
+  r.outer_iters = f.outer;
+  r.status = (f.phase == PH_DONE) ? f.status : SPAI_ERR_NOT_CONVERGED;
+  r.true_rel_res = true_rel;
+  r.rec_rel_res = f.bb > 0 ? sqrt(f.rr / f.bb) : 0.0;
+  r.history_written = f.hist_n;
+  r.engine_ms = engine_ms;
+  r.slots = slots;
+  r.launches = launches;
+}
+
+// Runs PCG on nsys systems in one persistent launch sequence.
+int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const double* const* b, double* const* x,
+               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override) {
+  if (nsys <= 0) return set_error(SPAI_ERR_INVALID, "nsys must be positive");
+  int rc;
+  if ((rc = engine_check_opts(o))) return rc;
+  const bool mixed = o->precision == SPAI_PREC_MIXED;
+  const int gtype = M[0]->gtype;
+  for (int i = 0; i < nsys; ++i) {
+    if (!S[i] || !M[i] || !b[i] || !x[i]) return set_error(SPAI_ERR_INVALID, "null system, preconditioner or vector");
+    if (M[i]->gtype != gtype) return set_error(SPAI_ERR_INVALID, "all preconditioners of a batch need one G type");
+    if (M[i]->P->n != S[i]->n) return set_error(SPAI_ERR_SHAPE, "G and A sizes differ (system %d)", i);
+  }
+  EngineBatch B;
+  if ((rc = B.init(mixed, gtype, *o, s))) return rc;
+  std::vector<DevMem> ws(nsys);
+  std::vector<EngineBatch::Member> mem(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    if ((rc = ws[i].alloc(engine_work_bytes(S[i]->n, mixed), s))) return rc;
+    EngineBatch::Member& m = mem[i];
+    m.S = S[i];
+    m.M = M[i];
+    m.b = b[i];
+    m.x = x[i];
+    m.work = ws[i].p;
+    m.history = (nsys == 1 && o->record_history) ? o->history : nullptr;
+    m.history_len = (nsys == 1 && o->record_history) ? o->history_len : 0;
+    m.st = EngineBatch::fresh_state(mixed);
+  }
+  if ((rc = B.set_members(mem, grid_override))) return rc;
+  const int64_t slot_cap = 8 * B.max_iter() + 64;
+  const int chunk = 3000;
+  int launches = 0;
+  double engine_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SPAI_CUDA(cudaEventCreate(&ev0));
+  SPAI_CUDA(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } evg{ev0, ev1};
+  while (B.live() > 0) {
+    const int64_t left = slot_cap - B.slots();
+    if (left <= 0) break;
+    if ((rc = B.launch((int)(left < chunk ? left : chunk), ev0, ev1, &engine_ms))) return rc;
+    ++launches;
+  }
+  std::vector<EngState> fin;
+  if ((rc = B.read_states(fin))) return rc;
+  std::vector<double> tr(nsys);
+  if ((rc = engine_true_residuals(nsys, S, b, x, tr.data(), s))) return rc;
+  int first_bad = SPAI_OK;
+  for (int i = 0; i < nsys; ++i) {
+    engine_fill_result(fin[i], tr[i], engine_ms, B.slots(), launches, res[i]);
+    if (res[i].status != SPAI_OK && first_bad == SPAI_OK) first_bad = res[i].status;
+  }
+  if (first_bad != SPAI_OK)
     set_error(first_bad, "pcg: %s", first_bad == SPAI_ERR_BREAKDOWN ? "breakdown" : "not converged");
-  }
   return first_bad;
 }
+
+}  // namespace spai
+
+// ---------------------------------------------------------------------------
+// Session interface used by the server: a batch whose members carry their
+// state (an opaque block of engine_state_bytes()) across launches.
+// ---------------------------------------------------------------------------
+namespace spai {
+
+struct SessionMember {
+  SystemData* S;
+  PrecondData* M;
+  const double* b;
+  double* x;
+  void* work;
+  std::vector<unsigned char> state;  // empty: start a new solve
+};
+struct SessionView {
+  bool done;
+  int status;
+  int64_t iters;
+  int outer;
+};
+struct EngineSession {
+  EngineBatch batch;
+  bool mixed;
+};
+
+size_t engine_state_bytes() { return sizeof(EngState); }
+
+int session_create(bool mixed, int gtype, const spai_pcg_opts& o, cudaStream_t s, EngineSession** out) {
+  int rc;
+  if ((rc = engine_check_opts(&o))) return rc;
+  auto* es = new EngineSession();
+  es->mixed = mixed;
+  if ((rc = es->batch.init(mixed, gtype, o, s))) {
+    delete es;
+    return rc;
+  }
+  *out = es;
+  return SPAI_OK;
+}
+
+int session_set(EngineSession* es, std::vector<SessionMember>& members) {
+  std::vector<EngineBatch::Member> mem(members.size());
+  for (size_t i = 0; i < members.size(); ++i) {
+    SessionMember& sm = members[i];
+    EngineBatch::Member& m = mem[i];
+    m.S = sm.S;
+    m.M = sm.M;
+    m.b = sm.b;
+    m.x = sm.x;
+    m.work = sm.work;
+    m.history = nullptr;
+    m.history_len = 0;
+    if (sm.state.size() == sizeof(EngState)) memcpy(&m.st, sm.state.data(), sizeof(EngState));
+    else m.st = EngineBatch::fresh_state(es->mixed);
+  }
+  return es->batch.set_members(mem);
+}
+
+int session_launch(EngineSession* es, int max_slots) { return es->batch.launch(max_slots, nullptr, nullptr, nullptr); }
+
+int session_live(EngineSession* es) { return es->batch.live(); }
+
+int session_read(EngineSession* es, std::vector<SessionMember>& members, std::vector<SessionView>& views) {
+  std::vector<EngState> st;
+  int rc;
+  if ((rc = es->batch.read_states(st))) return rc;
+  views.resize(st.size());
+  for (size_t i = 0; i < st.size(); ++i) {
+    members[i].state.resize(sizeof(EngState));
+    memcpy(members[i].state.data(), &st[i], sizeof(EngState));
+    views[i].done = st[i].phase == PH_DONE;
+    views[i].status = st[i].status;
+    views[i].iters = st[i].iter;
+    views[i].outer = st[i].outer;
+  }
+  return SPAI_OK;
+}
+
+void session_destroy(EngineSession* es) { delete es; }
 
 }  // namespace spai
 
