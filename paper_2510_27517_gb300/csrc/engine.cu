@@ -122,13 +122,16 @@ template <> struct Conv<float> {
   template <class U> __device__ static float f(U v) { return to_f32(v); }
 };
 
-constexpr int kBlock = 512;   // threads per block
-constexpr int kNE = 4;        // staged entries per thread per group
+constexpr int kBlock = 256;   // threads per block
+constexpr int kNE = 8;        // staged entries per thread per group
 constexpr int kCap = kNE * kBlock;
 constexpr int kRMax = 1;      // rows per thread whose operands are loaded together
 constexpr int kChunk = 32;    // items per first-level reduction chunk
-constexpr int kStages = 3;    // TMA stage ring depth
+constexpr int kStages32 = 3;  // TMA stage ring depth (float32 kernels)
+constexpr int kStages64 = 2;  // TMA stage ring depth (float64 kernels)
+constexpr int kStages = 4;    // largest ring (shared-memory arrays)
 constexpr int kMaxK = 64;     // groups per work item at most
+constexpr int kWarpE = 256;   // entries per warp product chunk
 constexpr int kAlignE = 8;    // bulk copies start at multiples of 8 entries (16 B for every type)
 
 // y_row = sum over the row's entries of val * op.gather(col), in stored
@@ -140,19 +143,7 @@ constexpr int kAlignE = 8;    // bulk copies start at multiples of 8 entries (16
 template <class AT, class MV, class Op>
 __device__ __forceinline__ void spmv_group(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                            const MV* __restrict__ val, int r, int re, int base, int m, AT* sbuf,
-                                           const Op& op, double& p0, double& p1) {
-  // operands of this thread's first rows: issued before the entry loads
-  typename Op::Pre pr[kRMax];
-  int ea[kRMax], eb[kRMax];
-#pragma unroll
-  for (int u = 0; u < kRMax; ++u) {
-    const int row = r + threadIdx.x + u * kBlock;
-    if (row < re) {
-      ea[u] = __ldg(rp + row) - base;
-      eb[u] = __ldg(rp + row + 1) - base;
-      pr[u] = op.pre(row);
-    }
-  }
+                                           const Op& op, double& p0, double& p1, uint32_t& blocks) {
   {
     int cix[kNE];
     AT v[kNE];
@@ -175,23 +166,22 @@ __device__ __forceinline__ void spmv_group(const int32_t* __restrict__ rp, const
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int u = 0; u < kRMax; ++u) {
-    const int row = r + threadIdx.x + u * kBlock;
+  // rows are dealt exactly as in the pipelined path: 32-row blocks to warps
+  // round-robin (continuing over the groups of an item), one row per lane
+  constexpr int NW = kBlock / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nblk = (re - r + 31) >> 5;
+  for (int j = (int)((uint32_t)(warp - (int)(blocks % NW) + NW) % NW); j < nblk; j += NW) {
+    const int row = r + 32 * j + lane;
     if (row < re) {
+      const int a0 = __ldg(rp + row) - base, a1 = __ldg(rp + row + 1) - base;
+      const typename Op::Pre q = op.pre(row);
       AT sum = AT(0);
-      for (int e = ea[u]; e < eb[u]; ++e) sum = radd(sum, sbuf[e]);
-      op.fin(row, sum, pr[u], p0, p1);
+      for (int e = a0; e < a1; ++e) sum = radd(sum, sbuf[e]);
+      op.fin(row, sum, q, p0, p1);
     }
   }
-  // rows beyond the first kRMax * kBlock (groups of very short rows)
-  for (int row = r + threadIdx.x + kRMax * kBlock; row < re; row += kBlock) {
-    const int a0 = __ldg(rp + row) - base, a1 = __ldg(rp + row + 1) - base;
-    const typename Op::Pre q = op.pre(row);
-    AT sum = AT(0);
-    for (int e = a0; e < a1; ++e) sum = radd(sum, sbuf[e]);
-    op.fin(row, sum, q, p0, p1);
-  }
+  blocks += (uint32_t)nblk;
   __syncthreads();
 }
 
@@ -204,10 +194,10 @@ __device__ __forceinline__ void spmv_group(const int32_t* __restrict__ rp, const
 template <class AT, class MV, class Op>
 __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                           const MV* __restrict__ val, int r0, int r1, AT* sbuf, double* red,
-                                          const Op& op, double& p0, double& p1) {
+                                          const Op& op, double& p0, double& p1, uint32_t& blocks) {
   const int t0 = __ldg(rp + r0), t1 = __ldg(rp + r1);
   if (t1 - t0 <= kCap) {
-    spmv_group<AT>(rp, ci, val, r0, r1, t0, t1 - t0, sbuf, op, p0, p1);
+    spmv_group<AT>(rp, ci, val, r0, r1, t0, t1 - t0, sbuf, op, p0, p1, blocks);
     return;
   }
   int r = r0;
@@ -233,7 +223,7 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
       r += 1;
       continue;
     }
-    spmv_group<AT>(rp, ci, val, r, re, base, __ldg(rp + re) - base, sbuf, op, p0, p1);
+    spmv_group<AT>(rp, ci, val, r, re, base, __ldg(rp + re) - base, sbuf, op, p0, p1, blocks);
     r = re;
   }
 }
@@ -243,10 +233,10 @@ template <class VT> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
   const VT* s; const VT* dcur; VT* dnxt; VT* q; VT beta; bool first;
   struct Pre { VT sv, dv; };
   __device__ VT gather(int c) const {
-    const VT sv = ldcg(s + c);
-    return first ? sv : radd(sv, rmul(beta, ldcg(dcur + c)));
+    const VT sv = ldv(s + c);
+    return first ? sv : radd(sv, rmul(beta, ldv(dcur + c)));
   }
-  __device__ Pre pre(int row) const { return Pre{ldcg(s + row), first ? VT(0) : ldcg(dcur + row)}; }
+  __device__ Pre pre(int row) const { return Pre{ldv(s + row), first ? VT(0) : ldv(dcur + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     const VT pv = first ? p.sv : radd(p.sv, rmul(beta, p.dv));
     dnxt[row] = pv;
@@ -257,8 +247,8 @@ template <class VT> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
 template <class VT> struct OpP2 {   // x += alpha d;  r' = r - alpha q;  t = G^T r';  r'.r'
   const VT* rcur; VT* rnxt; const VT* q; const VT* dcur; VT* x; VT* t; VT alpha;
   struct Pre { VT xv, dv, rv, qv; };
-  __device__ VT gather(int c) const { return rsub(ldcg(rcur + c), rmul(alpha, ldcg(q + c))); }
-  __device__ Pre pre(int row) const { return Pre{ldcg(x + row), ldcg(dcur + row), ldcg(rcur + row), ldcg(q + row)}; }
+  __device__ VT gather(int c) const { return rsub(ldv(rcur + c), rmul(alpha, ldv(q + c))); }
+  __device__ Pre pre(int row) const { return Pre{ldv(x + row), ldv(dcur + row), ldv(rcur + row), ldv(q + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     x[row] = radd(p.xv, rmul(alpha, p.dv));
     const VT rn = rsub(p.rv, rmul(alpha, p.qv));
@@ -270,15 +260,15 @@ template <class VT> struct OpP2 {   // x += alpha d;  r' = r - alpha q;  t = G^T
 template <class VT> struct OpApply1 {   // t = G^T r
   const VT* r; VT* t;
   struct Pre {};
-  __device__ VT gather(int c) const { return ldcg(r + c); }
+  __device__ VT gather(int c) const { return ldv(r + c); }
   __device__ Pre pre(int) const { return Pre{}; }
   __device__ void fin(int row, VT sum, const Pre&, double&, double&) const { t[row] = sum; }
 };
 template <class VT> struct OpApply2 {   // s = G t + eps r;  r.s
   const VT* t; const VT* r; VT* s; VT eps;
   struct Pre { VT rv; };
-  __device__ VT gather(int c) const { return ldcg(t + c); }
-  __device__ Pre pre(int row) const { return Pre{ldcg(r + row)}; }
+  __device__ VT gather(int c) const { return ldv(t + c); }
+  __device__ Pre pre(int row) const { return Pre{ldv(r + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     const VT sv = radd(sum, rmul(eps, p.rv));
     s[row] = sv;
@@ -288,7 +278,7 @@ template <class VT> struct OpApply2 {   // s = G t + eps r;  r.s
 template <class VT> struct OpResid {   // r = b - A x;  r.r, b.b   (b float64)
   const VT* x; const double* b; VT* r;
   struct Pre { double bv; };
-  __device__ VT gather(int c) const { return ldcg(x + c); }
+  __device__ VT gather(int c) const { return ldv(x + c); }
   __device__ Pre pre(int row) const { return Pre{__ldg(b + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double& p1) const {
     const VT rv = rsub((VT)p.bv, sum);
@@ -300,8 +290,8 @@ template <class VT> struct OpResid {   // r = b - A x;  r.r, b.b   (b float64)
 template <class VT> struct OpResidIn {   // r = rin - A e   (inner replacement, mixed)
   const VT* e; const VT* rin; VT* r;
   struct Pre { VT iv; };
-  __device__ VT gather(int c) const { return ldcg(e + c); }
-  __device__ Pre pre(int row) const { return Pre{ldcg(rin + row)}; }
+  __device__ VT gather(int c) const { return ldv(e + c); }
+  __device__ Pre pre(int row) const { return Pre{ldv(rin + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     const VT rv = rsub(p.iv, sum);
     r[row] = rv;
@@ -311,7 +301,7 @@ template <class VT> struct OpResidIn {   // r = rin - A e   (inner replacement, 
 template <class VT> struct OpResid64 {   // r64 = b - A64 x64;  r = rin = (VT) r64;  e = 0
   const double* x64; const double* b; VT* r; VT* rin; VT* e;
   struct Pre { double bv; };
-  __device__ double gather(int c) const { return ldcg(x64 + c); }
+  __device__ double gather(int c) const { return ldv(x64 + c); }
   __device__ Pre pre(int row) const { return Pre{__ldg(b + row)}; }
   __device__ void fin(int row, double sum, const Pre& p, double& p0, double& p1) const {
     const double r64 = __dsub_rn(p.bv, sum);
@@ -332,10 +322,11 @@ template <class MV> struct StageLayout {
   static constexpr int kColBytes = kStageE * 4;
   static constexpr int kValBytes = kStageE * (int)sizeof(MV);
   static constexpr int kStageBytes = kColBytes + kValBytes;
+  static constexpr int kStages = sizeof(MV) == 4 ? kStages32 : kStages64;
 };
 
 struct GroupHdr {
-  int r, re, e0, e0a, e1;
+  int r, re, e0, e0a, e1, r_al, staged, pad;
 };
 
 struct Pipe {
@@ -346,21 +337,23 @@ struct Pipe {
   GroupHdr* hdr;              // kStages headers
   int* grow;                  // kMaxK + 1 group row starts of the current item
   int* gent;                  // kMaxK + 1 group first entries
+  int* rel;                   // kStages release counters (warps done with the stage's group)
+  unsigned char* wbuf;        // per-warp product buffers (kWarpE entries of 8 bytes each)
   uint32_t issued, consumed;  // groups issued / consumed by this block (uniform)
+  uint32_t blocks_seen;       // 32-row blocks of all groups consumed so far (uniform)
 };
 
 // Thread 0: bulk-copy the entries of group g (rows tiles[g]..tiles[g+1]) into
 // the next stage.  Copies start at a multiple of kAlignE entries (16-byte
 // aligned for every value type) and the arrays are padded past nnz.
 template <class MV>
-__device__ __forceinline__ void issue_group(Pipe& P, const int32_t* ci, const MV* val, int k) {
-  const int st = (int)(P.issued % kStages);
+__device__ __forceinline__ void issue_group(Pipe& P, const int32_t* ci, const MV* val, int k, int st) {
   const int r = P.grow[k], re = P.grow[k + 1];
   const int e0 = P.gent[k], e1 = P.gent[k + 1];
   const int e0a = e0 & ~(kAlignE - 1);
   int ne = ((e1 + kAlignE - 1) & ~(kAlignE - 1)) - e0a;
   if (ne < kAlignE) ne = kAlignE;
-  P.hdr[st] = GroupHdr{r, re, e0, e0a, e1};
+  P.hdr[st] = GroupHdr{r, re, e0, e0a, e1, 0, 0, 0};
   unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
   const unsigned cb = (unsigned)ne * 4u, vb = (unsigned)ne * (unsigned)sizeof(MV);
   mbar_arrive_expect_tx(P.bar + st, cb + vb);
@@ -369,97 +362,105 @@ __device__ __forceinline__ void issue_group(Pipe& P, const int32_t* ci, const MV
   tma_load_1d_hint(base + P.col_bytes, val + e0a, vb, P.bar + st, pol);
 }
 
-// Processes groups [g0, g1) of one matrix through the stage ring, software
-// pipelined across groups: while the products of group k are gathered
-// (column indices from the stage buffer, vector entries from L2), the row
-// operands of group k-1 are loaded, and then group k-1's rows are summed from
-// the other product buffer.  One round trip to L2 per group.
-template <class AT, class MV, class Op>
+// Processes groups [g0, g1) of one matrix through the stage ring.  Warps work
+// independently: each takes 32-row blocks of every staged group (blocks are
+// dealt round-robin over the warps, continuing across groups), one row per
+// lane for the sums and all 32 lanes for the entry gathers, with a private
+// product buffer and only warp-level synchronisation.  A stage is released
+// when every warp is done with its group; the warp that releases it last
+// issues the bulk copy of the group kStages further on into it.
+template <int NS, class AT, class MV, class Op>
 __device__ __forceinline__ void piped_groups(Pipe& P, const int32_t* __restrict__ tiles,
                                              const int32_t* __restrict__ rp, const int32_t* ci, const MV* val,
-                                             int g0, int g1, AT* sbuf, const Op& op, double& p0, double& p1,
+                                             int g0, int g1, const Op& op, double& p0, double& p1,
                                              uint64_t limit_ns, int* err) {
   const int ng = g1 - g0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kBlock / 32;
   // bounds of every group of this item (row start, first entry), loaded once
   for (int i = threadIdx.x; i <= ng; i += blockDim.x) {
     const int r = __ldg(tiles + g0 + i);
     P.grow[i] = r;
     P.gent[i] = __ldg(rp + r);
   }
+  if (threadIdx.x < NS) P.rel[threadIdx.x] = 0;
   __syncthreads();
+  const uint32_t c0 = P.consumed;
   if (threadIdx.x == 0) {
-    const int pre = ng < kStages ? ng : kStages;
-    for (int k = 0; k < pre; ++k) {
-      issue_group<MV>(P, ci, val, k);
-      P.issued++;
-    }
+    const int pre = ng < NS ? ng : NS;
+    for (int k = 0; k < pre; ++k) issue_group<MV>(P, ci, val, k, (int)((c0 + k) % NS));
   }
-  GroupHdr prev{0, 0, 0, 0, 0};
-  for (int k = 0; k <= ng; ++k) {
-    // row operands of group k-1 (summed below)
-    typename Op::Pre pr;
-    int ea = 0, eb = 0;
-    const int row = prev.r + threadIdx.x;
-    const bool has_row = (k > 0) && row < prev.re;
-    if (has_row) {
-      ea = __ldg(rp + row) - prev.e0;
-      eb = __ldg(rp + row + 1) - prev.e0;
-      pr = op.pre(row);
-    }
-    GroupHdr h{0, 0, 0, 0, 0};
-    if (k < ng) {
-      const int st = (int)(P.consumed % kStages);
-      const unsigned parity = (P.consumed / kStages) & 1u;
-      if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
-      P.consumed++;
-      h = P.hdr[st];
-      const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
-      const int32_t* cs = reinterpret_cast<const int32_t*>(base) + (h.e0 - h.e0a);
-      const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) + (h.e0 - h.e0a);
-      const int m = h.e1 - h.e0;
-      AT* pb = sbuf + (k & 1) * kCap;
-      int cix[kNE];
+  AT* wb = reinterpret_cast<AT*>(P.wbuf) + warp * kWarpE;
+  uint32_t blocks = 0;  // the deal of row blocks to warps restarts with every item
+  for (int k = 0; k < ng; ++k) {
+    const uint32_t c = c0 + k;
+    const int st = (int)(c % NS);
+    const unsigned parity = (c / NS) & 1u;
+    if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
+    const GroupHdr h = P.hdr[st];
+    const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+    const int32_t* cs = reinterpret_cast<const int32_t*>(base) - h.e0a;  // indexed by entry offset
+    const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) - h.e0a;
+    const int nrows = h.re - h.r;
+    const int nblk = (nrows + 31) >> 5;
+    // first block of this group owned by this warp
+    int j = (int)((uint32_t)(warp - (int)(blocks % NW) + NW) % NW);
+    for (; j < nblk; j += NW) {
+      const int row = h.r + 32 * j + lane;
+      const bool valid = row < h.re;
+      int ea = 0, eb = 0;
+      typename Op::Pre pr;
+      if (valid) {
+        ea = __ldg(rp + row);
+        eb = __ldg(rp + row + 1);
+        pr = op.pre(row);
+      }
+      const int last = min(31, h.re - (h.r + 32 * j) - 1);
+      const int E0 = __shfl_sync(0xffffffffu, ea, 0);
+      const int E1 = __shfl_sync(0xffffffffu, eb, last);
+      AT acc = AT(0);
+      for (int cb = E0; cb < E1; cb += kWarpE) {
+        const int m = min(kWarpE, E1 - cb);
+        int cix[kWarpE / 32];
 #pragma unroll
-      for (int u = 0; u < kNE; ++u) {
-        const int kk = threadIdx.x + u * kBlock;
-        cix[u] = (kk < m) ? cs[kk] : 0;
-      }
-      AT g[kNE];
+        for (int u = 0; u < kWarpE / 32; ++u) {
+          const int kk = lane + 32 * u;
+          cix[u] = (kk < m) ? cs[cb + kk] : 0;
+        }
+        AT g[kWarpE / 32];
 #pragma unroll
-      for (int u = 0; u < kNE; ++u) {
-        const int kk = threadIdx.x + u * kBlock;
-        g[u] = (kk < m) ? op.gather(cix[u]) : AT(0);
-      }
+        for (int u = 0; u < kWarpE / 32; ++u) {
+          const int kk = lane + 32 * u;
+          g[u] = (kk < m) ? op.gather(cix[u]) : AT(0);
+        }
 #pragma unroll
-      for (int u = 0; u < kNE; ++u) {
-        const int kk = threadIdx.x + u * kBlock;
-        if (kk < m) pb[kk] = rmul(Conv<AT>::f(vs[kk]), g[u]);
+        for (int u = 0; u < kWarpE / 32; ++u) {
+          const int kk = lane + 32 * u;
+          if (kk < m) wb[kk] = rmul(Conv<AT>::f(vs[cb + kk]), g[u]);
+        }
+        __syncwarp();
+        if (valid) {
+          const int lo = max(ea, cb), hi = min(eb, cb + m);
+          for (int e = lo; e < hi; ++e) acc = radd(acc, wb[e - cb]);
+        }
+        __syncwarp();
+      }
+      if (valid) op.fin(row, acc, pr, p0, p1);
+    }
+    blocks += (uint32_t)nblk;
+    // release the stage; the last warp refills it
+    if (lane == 0) {
+      __threadfence_block();
+      const int prev = atomicAdd(P.rel + st, 1);
+      if (prev == NW - 1) {
+        P.rel[st] = 0;
+        if (k + NS < ng) issue_group<MV>(P, ci, val, k + NS, st);
       }
     }
-    if (has_row) {
-      const AT* qb = sbuf + ((k - 1) & 1) * kCap;
-      AT sum = AT(0);
-      for (int e = ea; e < eb; ++e) sum = radd(sum, qb[e]);
-      op.fin(row, sum, pr, p0, p1);
-    }
-    if (k > 0) {
-      // rows of group k-1 beyond one per thread
-      for (int rr = prev.r + threadIdx.x + kBlock; rr < prev.re; rr += kBlock) {
-        const int a0 = __ldg(rp + rr) - prev.e0, a1 = __ldg(rp + rr + 1) - prev.e0;
-        const typename Op::Pre q = op.pre(rr);
-        const AT* qb = sbuf + ((k - 1) & 1) * kCap;
-        AT sum = AT(0);
-        for (int e = a0; e < a1; ++e) sum = radd(sum, qb[e]);
-        op.fin(rr, sum, q, p0, p1);
-      }
-    }
-    __syncthreads();  // products of group k complete; stage of group k and products of k-1 free
-    if (k < ng && threadIdx.x == 0 && k + kStages < ng) {
-      issue_group<MV>(P, ci, val, k + kStages);
-      P.issued++;
-    }
-    prev = h;
+    __syncwarp();
   }
+  P.consumed = c0 + ng;
+  __syncthreads();
 }
 
 // Groups [g0, g1) without the stage ring (rows longer than a group, or the
@@ -468,8 +469,9 @@ template <class AT, class MV, class Op>
 __device__ __noinline__ void direct_groups(const int32_t* __restrict__ tiles, const int32_t* __restrict__ rp,
                                               const int32_t* __restrict__ ci, const MV* __restrict__ val, int g0,
                                               int g1, AT* sbuf, double* red, const Op& op, double& p0, double& p1) {
+  uint32_t blocks = 0;
   for (int g = g0; g < g1; ++g)
-    spmv_rows<AT>(rp, ci, val, __ldg(tiles + g), __ldg(tiles + g + 1), sbuf, red, op, p0, p1);
+    spmv_rows<AT>(rp, ci, val, __ldg(tiles + g), __ldg(tiles + g + 1), sbuf, red, op, p0, p1, blocks);
 }
 
 template <class AT, class MV, class Op>
@@ -477,7 +479,8 @@ __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* t
                                            const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
                                            double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
                                            int* err) {
-  if (piped) piped_groups<AT, MV>(P, tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), op, p0, p1, limit_ns, err);
+  if (piped) piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0,
+                                                                              p1, limit_ns, err);
   else direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op, p0, p1);
 }
 
@@ -545,9 +548,9 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
     case PH_ZEROX: {
       const int r0 = __ldg(tl + g0), r1 = __ldg(tl + g1);
       for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-        if (ph == PH_P2X) xv[row] = radd(ldcg(xv + row), rmul(alpha, ldcg(d_cur + row)));
+        if (ph == PH_P2X) xv[row] = radd(ldv(xv + row), rmul(alpha, ldv(d_cur + row)));
         else if (ph == PH_XUPD) {
-          S.x[row] = __dadd_rn(ldcg(S.x + row), (double)ldcg(xv + row));
+          S.x[row] = __dadd_rn(ldv(S.x + row), (double)ldv(xv + row));
           xv[row] = VT(0);
         }
         else S.x[row] = 0.0;
@@ -688,16 +691,17 @@ __device__ __forceinline__ void load_state(const EngState* src, EngState* dst) {
 }
 
 template <class VT, class GT, bool MIXED>
-__global__ void __launch_bounds__(kBlock, 1) engine_kernel(EngArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   using MVmax = typename std::conditional<MIXED, float, double>::type;
   using L = StageLayout<MVmax>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ double red[64];
   __shared__ int sflag, s_last;
   __shared__ EngState s_st;
   __shared__ uint64_t s_bar[kStages];
   __shared__ GroupHdr s_hdr[kStages];
   __shared__ int s_grow[kMaxK + 1], s_gent[kMaxK + 1];
+  __shared__ int s_rel[kStages];
 
   Pipe P;
   P.stage_base = smem_raw;
@@ -707,11 +711,14 @@ __global__ void __launch_bounds__(kBlock, 1) engine_kernel(EngArgs a) {
   P.hdr = s_hdr;
   P.grow = s_grow;
   P.gent = s_gent;
+  P.rel = s_rel;
   P.issued = 0;
   P.consumed = 0;
-  void* sbuf = smem_raw + (size_t)kStages * L::kStageBytes;
+  P.blocks_seen = 0;
+  void* sbuf = smem_raw + (size_t)L::kStages * L::kStageBytes;
+  P.wbuf = static_cast<unsigned char*>(sbuf);  // shared with the direct path's buffer (never used at once)
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(s_bar + i, 1);
+    for (int i = 0; i < L::kStages; ++i) mbar_init(s_bar + i, 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -741,8 +748,7 @@ __global__ void __launch_bounds__(kBlock, 1) engine_kernel(EngArgs a) {
       if (g1 > S.ntiles[m]) g1 = S.ntiles[m];
       double p0 = 0.0, p1 = 0.0;
       if (g0 < g1) run_item<VT, GT, MIXED>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err);
-      p0 = block_sum(p0, red);
-      p1 = block_sum(p1, red);
+      block_sum2(p0, p1, red);
       double* pbase = a.partial + 2 * (size_t)S.item_base;
       double* cbase = a.cpartial + 2 * (size_t)S.chunk_base;
       const int nit = S.nitems;
@@ -752,15 +758,13 @@ __global__ void __launch_bounds__(kBlock, 1) engine_kernel(EngArgs a) {
       if (threadIdx.x == 0) {
         pbase[2 * v] = p0;
         pbase[2 * v + 1] = p1;
-        __threadfence();
-        const unsigned prev = atomicAdd(a.ccnt + S.chunk_base + ch, 1u);
+        const unsigned prev = atom_add_acq_rel_u32(a.ccnt + S.chunk_base + ch, 1u);
         s_last = (prev == (unsigned)(ch_size - 1)) ? 1 : 0;
       }
       __syncthreads();
       if (s_last) {
         // this block completed chunk `ch`: sum its item partials (one warp, fixed tree)
         if (threadIdx.x < 32) {
-          __threadfence();
           const int tt = ch * kChunk + threadIdx.x;
           double c0 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt) : 0.0;
           double c1 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt + 1) : 0.0;
@@ -770,28 +774,24 @@ __global__ void __launch_bounds__(kBlock, 1) engine_kernel(EngArgs a) {
             cbase[2 * ch] = c0;
             cbase[2 * ch + 1] = c1;
             a.ccnt[S.chunk_base + ch] = 0u;
-            __threadfence();
-            const unsigned prev = atomicAdd(a.cnt + sid, 1u);
+            const unsigned prev = atom_add_acq_rel_u32(a.cnt + sid, 1u);
             s_last = (prev == (unsigned)(nch - 1)) ? 2 : 0;
           }
         }
         __syncthreads();
         if (s_last == 2) {
-          __threadfence();
           double q0 = 0.0, q1 = 0.0;
           for (int tt = threadIdx.x; tt < nch; tt += blockDim.x) {
             q0 += __ldcg(cbase + 2 * tt);
             q1 += __ldcg(cbase + 2 * tt + 1);
           }
-          q0 = block_sum(q0, red);
-          q1 = block_sum(q1, red);
+          block_sum2(q0, q1, red);
           if (threadIdx.x == 0) {
             EngState ns = s_st;
             transition<MIXED>(S, ns, q0, q1, a.o, a.gs);
             nxt[sid] = ns;
             if (ns.phase == PH_DONE) cur[sid] = ns;
             a.cnt[sid] = 0u;
-            __threadfence();
           }
         }
       }
@@ -845,8 +845,10 @@ const void* select_kernel(bool mixed, int gtype) {
 }  // namespace
 
 size_t engine_smem_bytes(bool mixed) {
-  const int stage = mixed ? StageLayout<float>::kStageBytes : StageLayout<double>::kStageBytes;
-  return (size_t)kStages * stage + 2 * (size_t)kCap * sizeof(double);
+  const int stage = mixed ? StageLayout<float>::kStageBytes * kStages32 : StageLayout<double>::kStageBytes * kStages64;
+  const size_t prod = (size_t)kCap * sizeof(double);                    // direct path
+  const size_t warp = (size_t)(kBlock / 32) * kWarpE * sizeof(double);  // pipelined path
+  return (size_t)stage + (prod > warp ? prod : warp);
 }
 
 bool engine_groups_fit(int32_t max_row) { return max_row >= 1 && max_row <= kCap / 2; }

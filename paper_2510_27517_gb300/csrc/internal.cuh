@@ -122,13 +122,28 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// Loads of data written earlier in the same kernel by other blocks: bypass L1.
+// Loads of vectors written by other blocks before the last grid barrier
+// (ordinary cached loads; the barrier's fences order them).
+template <class T> __device__ __forceinline__ T ldv(const T* p) { return *p; }
+
+// Loads of data written earlier in the same kernel by other blocks without an
+// intervening grid barrier (reduction partials, states): bypass L1.
 template <class T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 template <> __device__ __forceinline__ __nv_bfloat16 ldcg(const __nv_bfloat16* p) {
   unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(p));
@@ -231,6 +246,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
+// Two deterministic block sums in one pass; `scratch` needs 2 * warps doubles.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) {
+    scratch[w] = a;
+    scratch[nw + w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double ta = (l < nw) ? scratch[l] : 0.0;
+    double tb = (l < nw) ? scratch[nw + l] : 0.0;
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    if (l == 0) {
+      scratch[0] = ta;
+      scratch[nw] = tb;
+    }
+  }
+  __syncthreads();
+  a = scratch[0];
+  b = scratch[nw];
+  __syncthreads();
+}
+
 // Grid-wide barrier for cooperative launches with a bounded wait.
 struct GridSync {
   unsigned count;
@@ -243,33 +285,34 @@ struct GridSync {
 };
 
 // Returns the exit flag decided at this barrier.  Every wait is bounded by
-// `limit_ns`; on expiry err is set and the caller must stop.
+// `limit_ns`; on expiry err is set and the caller must stop.  Arrival is an
+// acq_rel atomic (releases this block's writes, and the last arriver acquires
+// everyone's); the last arriver publishes the next generation with a release
+// store and the others acquire it, so writes made before the barrier by any
+// block are visible after it (the CTA barrier extends this to every thread).
 __device__ __forceinline__ int grid_barrier(GridSync* g, unsigned nblocks, uint64_t limit_ns, int* sflag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned my_gen = ld_acquire_u32(&g->gen);
-    __threadfence();
-    unsigned prev = atomicAdd(&g->count, 1u);
+    const unsigned my_gen = ld_relaxed_u32(&g->gen);
+    const unsigned prev = atom_add_acq_rel_u32(&g->count, 1u);
     if (prev == nblocks - 1) {
       g->count = 0;
-      int live = *(volatile int*)&g->live;
-      int err = *(volatile int*)&g->err;
+      const int live = *(volatile int*)&g->live;
+      const int err = *(volatile int*)&g->err;
       *(volatile int*)&g->exit_flag = (live <= 0 || err != 0) ? 1 : 0;
-      __threadfence();
       st_release_u32(&g->gen, my_gen + 1u);
     } else {
       const uint64_t t0 = global_ns();
       unsigned spins = 0;
       while (ld_acquire_u32(&g->gen) == my_gen) {
-        __nanosleep(32);
-        if ((++spins & 255u) == 0 && global_ns() - t0 > limit_ns) {
+        if ((++spins & 1023u) == 0 && global_ns() - t0 > limit_ns) {
           atomicExch(&g->err, SPAI_ERR_TIMEOUT);
           break;
         }
       }
     }
-    int ef = *(volatile int*)&g->exit_flag;
-    int er = *(volatile int*)&g->err;
+    const int ef = *(volatile int*)&g->exit_flag;
+    const int er = *(volatile int*)&g->err;
     *sflag = (ef || er) ? 1 : 0;
   }
   __syncthreads();

@@ -322,7 +322,7 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
   if (kind == SPAI_PATTERN_FULL) {
     P->nnz = A->nnz;
     P->max_row = P->max_row_t = max_row;
-    if ((rc = P->rowptr.alloc((n + 1) * sizeof(int32_t), s))) return rc;
+    if ((rc = P->rowptr.alloc((n + 1 + 16) * sizeof(int32_t), s))) return rc;
     if ((rc = P->colidx.alloc((A->nnz + 16) * sizeof(int32_t), s))) return rc;
     if ((rc = P->perm.alloc((A->nnz + 1) * sizeof(int32_t), s))) return rc;
     SPAI_CUDA(cudaMemcpyAsync(P->rowptr.p, A->rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
@@ -335,12 +335,12 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
     DevMem cnt;
     if ((rc = cnt.alloc((n + 1) * sizeof(int32_t), s))) return rc;
     // G
-    if ((rc = P->rowptr.alloc((n + 1) * sizeof(int32_t), s))) return rc;
+    if ((rc = P->rowptr.alloc((n + 1 + 16) * sizeof(int32_t), s))) return rc;
     count_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, lower_g, cnt.as<int32_t>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     if ((rc = exclusive_scan_i32(cnt.as<int32_t>(), P->rowptr.as<int32_t>(), n + 1, s))) return rc;
     // G^T: the other triangle (the pattern of A is symmetric)
-    if ((rc = P->t_rowptr.alloc((n + 1) * sizeof(int32_t), s))) return rc;
+    if ((rc = P->t_rowptr.alloc((n + 1 + 16) * sizeof(int32_t), s))) return rc;
     count_tri_kernel<<<grid_for(n, block), block, 0, s>>>(A->rowptr, A->colidx, n, 1 - lower_g, cnt.as<int32_t>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     if ((rc = exclusive_scan_i32(cnt.as<int32_t>(), P->t_rowptr.as<int32_t>(), n + 1, s))) return rc;
