@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "gnn_tc.cuh"
 
 namespace spai {
 
@@ -35,34 +36,6 @@ namespace {
 constexpr int H = 24;        // hidden width d (Sec. 4.1)
 constexpr int MAXD = 16;     // largest node feature width accepted
 constexpr int ECAP = 256;    // edges staged per group (= block size)
-
-struct PQW {
-  float Wa[H * H];
-  float Wb[H * H];
-  float b[H];
-};
-
-struct NodeEncParams {
-  float W1[H * MAXD];
-  float b1[H];
-  float W2[H * H];
-  float b2[H];
-  PQW m;          // first layer split of f_m of layer 1
-  int d_node;
-  int has_m;
-};
-
-struct NodeLayerParams {
-  float W2m[H * H];
-  float b2m[H];
-  float W1v[H * H];
-  float b1v[H];
-  float W2v[H * H];
-  float b2v[H];
-  PQW e;          // f_e of this layer
-  PQW m;          // f_m of the next layer
-  int has_m;
-};
 
 struct EdgeParams {
   // encoder E_e (first pass only)
@@ -251,98 +224,241 @@ __global__ void __launch_bounds__(ECAP) edge_kernel(const EdgeArgs a, const __gr
   }
 }
 
-__device__ __forceinline__ void pq_store(const PQW& p, const float* x, float* out) {
-#pragma unroll
-  for (int o = 0; o < H; ++o) {
-    float a = 0.f, b = 0.f;
-#pragma unroll
-    for (int q = 0; q < H; ++q) {
-      a = fmaf(p.Wa[o * H + q], x[q], a);
-      b = fmaf(p.Wb[o * H + q], x[q], b);
-    }
-    out[o] = a + p.b[o];
-    out[H + o] = b;
-  }
-}
+// ---- per-node MLP layers on the tensor cores (tcgen05, 3xTF32) ----
+//
+// Weights of one kernel launch live in a device blob prepared on the host:
+// for every layer the B operand (N x K, K-major no-swizzle tile) as TF32 hi
+// and lo parts, and the bias.  Each block copies the blob to shared memory,
+// then walks 128-node tiles: the activations of the tile are written (split
+// into hi and lo) as the A operand, one thread issues the MMAs, every thread
+// reads its node's row of the accumulator back from tensor memory.
+struct TcLayer {
+  int K, N;          // padded sizes (K multiple of 8, N multiple of 16)
+  int b_hi, b_lo;    // float offsets of the B tiles in the blob
+  int bias;          // float offset of the bias (N floats)
+};
+struct TcNodeParams {
+  TcLayer L[5];
+  int nlayers;
+  int blob_floats;
+  int d_node;        // encoder only
+  int has_m;
+};
 
-__global__ void __launch_bounds__(128) node_enc_kernel(const float* __restrict__ v, int64_t n, float* x,
-                                                       float* PQm, const __grid_constant__ NodeEncParams w) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float in[MAXD];
+constexpr int kTcThreads = tc::kM;
+
+__device__ __forceinline__ void stage_a(float* a_hi, float* a_lo, const float* v, int K) {
+  const int row = threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < MAXD; ++k) in[k] = (k < w.d_node) ? __ldg(v + i * w.d_node + k) : 0.f;
-    float u[H], xo[H];
-#pragma unroll
-    for (int o = 0; o < H; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k < MAXD; ++k) acc = fmaf(w.W1[o * MAXD + k], in[k], acc);
-      u[o] = fmaxf(acc + w.b1[o], 0.f);
-    }
-#pragma unroll
-    for (int o = 0; o < H; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 0; q < H; ++q) acc = fmaf(w.W2[o * H + q], u[q], acc);
-      xo[o] = acc + w.b2[o];
-    }
-    float4* xp = reinterpret_cast<float4*>(x + i * H);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) xp[k] = make_float4(xo[4 * k], xo[4 * k + 1], xo[4 * k + 2], xo[4 * k + 3]);
-    if (w.has_m) {
-      float pq[2 * H];
-      pq_store(w.m, xo, pq);
-      float4* pp = reinterpret_cast<float4*>(PQm + i * 2 * H);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) pp[k] = make_float4(pq[4 * k], pq[4 * k + 1], pq[4 * k + 2], pq[4 * k + 3]);
+  for (int k = 0; k < H; ++k) {
+    if (k < K) {
+      const float hi = tc::tf32_rna(v[k]);
+      const int off = tc::core_off(row, k, K) >> 2;
+      a_hi[off] = hi;
+      a_lo[off] = tc::tf32_rna(v[k] - hi);
     }
   }
 }
 
-__global__ void __launch_bounds__(128) node_layer_kernel(const int32_t* __restrict__ rp, int64_t n,
-                                                         const float* __restrict__ S, float* x, float* PQe,
-                                                         float* PQm, const __grid_constant__ NodeLayerParams w) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float deg = (float)(__ldg(rp + i + 1) - __ldg(rp + i));
-    float s[H], m[H], u[H], xv[H];
-    load24(S + i * H, s);
-    load24(x + i * H, xv);
-#pragma unroll
-    for (int o = 0; o < H; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 0; q < H; ++q) acc = fmaf(w.W2m[o * H + q], s[q], acc);
-      m[o] = acc + deg * w.b2m[o];
-    }
-#pragma unroll
-    for (int o = 0; o < H; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 0; q < H; ++q) acc = fmaf(w.W1v[o * H + q], m[q], acc);
-      u[o] = fmaxf(acc + w.b1v[o], 0.f);
-    }
-#pragma unroll
-    for (int o = 0; o < H; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 0; q < H; ++q) acc = fmaf(w.W2v[o * H + q], u[q], acc);
-      xv[o] = xv[o] + (acc + w.b2v[o]);
-    }
-    float4* xp = reinterpret_cast<float4*>(x + i * H);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) xp[k] = make_float4(xv[4 * k], xv[4 * k + 1], xv[4 * k + 2], xv[4 * k + 3]);
-    float pq[2 * H];
-    pq_store(w.e, xv, pq);
-    float4* pe = reinterpret_cast<float4*>(PQe + i * 2 * H);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) pe[k] = make_float4(pq[4 * k], pq[4 * k + 1], pq[4 * k + 2], pq[4 * k + 3]);
-    if (w.has_m) {
-      pq_store(w.m, xv, pq);
-      float4* pm = reinterpret_cast<float4*>(PQm + i * 2 * H);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) pm[k] = make_float4(pq[4 * k], pq[4 * k + 1], pq[4 * k + 2], pq[4 * k + 3]);
-    }
+// Issues layer l on A (already staged) and waits; returns false on timeout.
+__device__ __forceinline__ bool tc_run_layer(const TcNodeParams& p, int l, const float* blob_s, uint32_t a_hi,
+                                             uint32_t a_lo, uint32_t tmem, uint64_t* bar, unsigned& phase,
+                                             int* err) {
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0) {
+    const TcLayer& L = p.L[l];
+    tc::gemm3(tmem, a_hi, a_lo, smem_u32(blob_s + L.b_hi), smem_u32(blob_s + L.b_lo), L.K, L.N);
+    tc::mma_commit(bar);
   }
+  const bool ok = tc::wait_phase(bar, phase, 2000000000ull);
+  phase ^= 1u;
+  tc::fence_after_sync();
+  if (!ok) atomicExch(err, SPAI_ERR_TIMEOUT);
+  return __syncthreads_or(ok ? 0 : 1) == 0;  // every thread leaves together on a timeout
+}
+
+// Reads `cnt` (multiple of 16) accumulator columns starting at col0 of this thread's row.
+__device__ __forceinline__ void tc_read(uint32_t tmem, int col0, int cnt, float* out) {
+  const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) * 32) << 16;
+  for (int c = 0; c < cnt; c += 16) tc::tmem_ld16(tmem + lane_base + (uint32_t)(col0 + c), out + c);
+}
+
+struct TcSmem {
+  float* blob;
+  float* a_hi;
+  float* a_lo;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ void tc_setup(const TcNodeParams& p, const float* __restrict__ blob_g, float* smem,
+                                         uint32_t* s_tmem, uint64_t* bar, TcSmem& t) {
+  t.a_hi = smem;
+  t.a_lo = smem + tc::kM * tc::kKmax;
+  t.blob = smem + 2 * tc::kM * tc::kKmax;
+  for (int i = threadIdx.x; i < p.blob_floats; i += blockDim.x) t.blob[i] = __ldg(blob_g + i);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(s_tmem)), "n"(tc::kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  t.tmem = *s_tmem;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(tc::kTmemCols) : "memory");
+}
+
+__device__ __forceinline__ void store24(float* dst, const float* v) {
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+
+// x = E_n(v);  PQm = first layer split of f_m of layer 1 (if has_m).
+// Layers: 0: relu(v W1^T + b1)  1: * W2^T + b2 (= x)  2: x [Wa;Wb]^T + [b;0]
+__global__ void __launch_bounds__(kTcThreads) node_enc_tc_kernel(const float* __restrict__ v, int64_t n, float* x,
+                                                                 float* PQm, const float* __restrict__ blob_g,
+                                                                 const __grid_constant__ TcNodeParams p, int* err) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  TcSmem t;
+  tc_setup(p, blob_g, smem, &s_tmem, &s_bar, t);
+  const uint32_t ahi = smem_u32(t.a_hi), alo = smem_u32(t.a_lo);
+  unsigned phase = 0;
+  const int64_t ntiles = (n + tc::kM - 1) / tc::kM;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row = tile * tc::kM + threadIdx.x;
+    const bool valid = row < n;
+    float in[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) in[k] = (valid && k < p.d_node) ? __ldg(v + row * p.d_node + k) : 0.f;
+    stage_a(t.a_hi, t.a_lo, in, p.L[0].K);
+    if (!tc_run_layer(p, 0, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+    float d[32];
+    tc_read(t.tmem, 0, 32, d);
+    float u[H];
+#pragma unroll
+    for (int o = 0; o < H; ++o) u[o] = fmaxf(d[o] + t.blob[p.L[0].bias + o], 0.f);
+    tc::fence_before_sync();
+    __syncthreads();
+    stage_a(t.a_hi, t.a_lo, u, H);
+    if (!tc_run_layer(p, 1, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+    tc_read(t.tmem, 0, 32, d);
+    float xo[H];
+#pragma unroll
+    for (int o = 0; o < H; ++o) xo[o] = d[o] + t.blob[p.L[1].bias + o];
+    if (valid) store24(x + row * H, xo);
+    if (p.has_m) {
+      tc::fence_before_sync();
+      __syncthreads();
+      stage_a(t.a_hi, t.a_lo, xo, H);
+      if (!tc_run_layer(p, 2, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+      float pq[48];
+      tc_read(t.tmem, 0, 48, pq);
+      if (valid) {
+        float o48[48];
+#pragma unroll
+        for (int o = 0; o < 48; ++o) o48[o] = pq[o] + t.blob[p.L[2].bias + o];
+        store24(PQm + row * 2 * H, o48);
+        store24(PQm + row * 2 * H + H, o48 + H);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  tc_teardown(t.tmem);
+}
+
+// One message-passing layer on the nodes:
+//   m = W2m S + deg b2m;  x += W2v relu(W1v m + b1v) + b2v;
+//   PQe = [Wea;Web] x + [be;0];  PQm = [Wma;Wmb] x + [bm;0] (next layer's f_m)
+// Layers: 0: S W2m^T  1: m W1v^T  2: u W2v^T  3: x [Wea;Web;Wma;Wmb]^T
+__global__ void __launch_bounds__(kTcThreads) node_layer_tc_kernel(const int32_t* __restrict__ rp, int64_t n,
+                                                                   const float* __restrict__ S, float* x, float* PQe,
+                                                                   float* PQm, const float* __restrict__ blob_g,
+                                                                   const __grid_constant__ TcNodeParams p, int* err) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  TcSmem t;
+  tc_setup(p, blob_g, smem, &s_tmem, &s_bar, t);
+  const uint32_t ahi = smem_u32(t.a_hi), alo = smem_u32(t.a_lo);
+  unsigned phase = 0;
+  const int64_t ntiles = (n + tc::kM - 1) / tc::kM;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row = tile * tc::kM + threadIdx.x;
+    const bool valid = row < n;
+    float sv[H], xv[H];
+    float deg = 0.f;
+    if (valid) {
+      load24(S + row * H, sv);
+      load24(x + row * H, xv);
+      deg = (float)(__ldg(rp + row + 1) - __ldg(rp + row));
+    } else {
+#pragma unroll
+      for (int k = 0; k < H; ++k) { sv[k] = 0.f; xv[k] = 0.f; }
+    }
+    stage_a(t.a_hi, t.a_lo, sv, H);
+    if (!tc_run_layer(p, 0, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+    float d[32], m[H];
+    tc_read(t.tmem, 0, 32, d);
+#pragma unroll
+    for (int o = 0; o < H; ++o) m[o] = d[o] + deg * t.blob[p.L[0].bias + o];
+    tc::fence_before_sync();
+    __syncthreads();
+    stage_a(t.a_hi, t.a_lo, m, H);
+    if (!tc_run_layer(p, 1, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+    tc_read(t.tmem, 0, 32, d);
+#pragma unroll
+    for (int o = 0; o < H; ++o) m[o] = fmaxf(d[o] + t.blob[p.L[1].bias + o], 0.f);
+    tc::fence_before_sync();
+    __syncthreads();
+    stage_a(t.a_hi, t.a_lo, m, H);
+    if (!tc_run_layer(p, 2, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+    tc_read(t.tmem, 0, 32, d);
+#pragma unroll
+    for (int o = 0; o < H; ++o) xv[o] = xv[o] + (d[o] + t.blob[p.L[2].bias + o]);
+    if (valid) store24(x + row * H, xv);
+    tc::fence_before_sync();
+    __syncthreads();
+    stage_a(t.a_hi, t.a_lo, xv, H);
+    if (!tc_run_layer(p, 3, t.blob, ahi, alo, t.tmem, &s_bar, phase, err)) break;
+    const int nout = p.L[3].N;  // 48 or 96
+    float pq[96];
+    tc_read(t.tmem, 0, 48, pq);
+    if (nout > 48) tc_read(t.tmem, 48, 48, pq + 48);
+    if (valid) {
+      float o48[48];
+#pragma unroll
+      for (int o = 0; o < 48; ++o) o48[o] = pq[o] + t.blob[p.L[3].bias + o];
+      store24(PQe + row * 2 * H, o48);
+      store24(PQe + row * 2 * H + H, o48 + H);
+      if (nout > 48) {
+#pragma unroll
+        for (int o = 0; o < 48; ++o) o48[o] = pq[48 + o] + t.blob[p.L[3].bias + 48 + o];
+        store24(PQm + row * 2 * H, o48);
+        store24(PQm + row * 2 * H + H, o48 + H);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  tc_teardown(t.tmem);
 }
 
 // ||A|| = mean |A_ij| in float64, deterministic two-level sum.
@@ -361,6 +477,46 @@ __global__ void abs_final_kernel(const double* part, int np, int64_t m, double* 
   s = block_sum(s, red);
   if (threadIdx.x == 0) out[0] = s / (double)m;
 }
+
+// TF32 rounding as the device's cvt.rna.tf32.f32: nearest, ties away from zero.
+float tf32_host(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+// Builds the weight blob of one tensor-core node kernel.
+struct TcBlob {
+  std::vector<float> f;
+  TcNodeParams p;
+  TcBlob() { memset(&p, 0, sizeof(p)); }
+  // rows[i] = pointer to the K_real inputs of output i (nullptr: zero row);
+  // bias[i] (nullptr: zero)
+  void add(const std::vector<const float*>& rows, int k_real, const std::vector<float>& bias) {
+    const int n_real = (int)rows.size();
+    const int N = ((n_real + 15) / 16) * 16, K = ((k_real + 7) / 8) * 8;
+    TcLayer& L = p.L[p.nlayers++];
+    L.K = K;
+    L.N = N;
+    L.b_hi = (int)f.size();
+    L.b_lo = L.b_hi + N * K;
+    L.bias = L.b_lo + N * K;
+    f.resize(f.size() + 2 * N * K + N, 0.f);
+    for (int r = 0; r < n_real; ++r)
+      for (int k = 0; k < k_real; ++k) {
+        const float w = rows[r] ? rows[r][k] : 0.f;
+        const float hi = tf32_host(w);
+        const int off = tc::core_off(r, k, K) >> 2;
+        f[L.b_hi + off] = hi;
+        f[L.b_lo + off] = tf32_host(w - hi);
+      }
+    for (int r = 0; r < (int)bias.size() && r < N; ++r) f[L.bias + r] = bias[r];
+    p.blob_floats = (int)f.size();
+  }
+};
 
 struct MLPView {
   const float* W1;
@@ -423,14 +579,6 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   auto fm = [&](int t) -> const MLPView& { return mv[2 + 3 * t]; };
   auto fv = [&](int t) -> const MLPView& { return mv[3 + 3 * t]; };
   auto fe = [&](int t) -> const MLPView& { return mv[4 + 3 * t]; };
-  auto split = [&](const MLPView& v, PQW& p) {
-    for (int o = 0; o < H; ++o)
-      for (int q = 0; q < H; ++q) {
-        p.Wa[o * H + q] = v.W1[o * v.fi + q];
-        p.Wb[o * H + q] = v.W1[o * v.fi + H + q];
-      }
-    for (int o = 0; o < H; ++o) p.b[o] = v.b1[o];
-  };
   auto edge_cols = [&](const MLPView& v, float* dst, int ncol) {
     for (int o = 0; o < H; ++o)
       for (int q = 0; q < ncol; ++q) dst[o * ncol + q] = v.W1[o * v.fi + 2 * H + q];
@@ -468,22 +616,48 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   TileSet et;
   if ((rc = build_tiles(P->g_rp(), n, nnz, 2048, et, s))) return rc;
 
-  const int nb = 128;
-  int ngrid = (int)((n + nb - 1) / nb);
-  if (ngrid > num_sms() * 32) ngrid = num_sms() * 32;
-  {
-    NodeEncParams p;
-    memset(&p, 0, sizeof(p));
-    for (int o = 0; o < H; ++o)
-      for (int k = 0; k < dn; ++k) p.W1[o * MAXD + k] = En.W1[o * dn + k];
-    memcpy(p.b1, En.b1, sizeof(p.b1));
-    memcpy(p.W2, En.W2, sizeof(p.W2));
-    memcpy(p.b2, En.b2, sizeof(p.b2));
-    p.d_node = dn;
-    p.has_m = L > 0;
-    if (L > 0) split(fm(0), p.m);
-    node_enc_kernel<<<ngrid, nb, 0, s>>>(node_feat, n, xbuf.as<float>(), pqm.as<float>(), p); count_launch();
+  // ---- tensor-core node kernels: launch configuration and weight blobs ----
+  const int64_t ntiles = (n + tc::kM - 1) / tc::kM;
+  int tgrid = (int)(ntiles < (int64_t)num_sms() * 3 ? ntiles : (int64_t)num_sms() * 3);
+  if (tgrid < 1) tgrid = 1;
+  DevMem tcerr, encblob;
+  if ((rc = tcerr.alloc(sizeof(int), s))) return rc;
+  SPAI_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), s));
+  auto rows_of = [&](const float* W, int ld, int col0, int nrows) {
+    std::vector<const float*> r(nrows);
+    for (int i = 0; i < nrows; ++i) r[i] = W + (size_t)i * ld + col0;
+    return r;
+  };
+  auto launch_tc = [&](auto kern, const TcBlob& tb, DevMem& blob, auto... args) -> int {
+    int rc2;
+    if ((rc2 = blob.alloc(tb.f.size() * sizeof(float), s))) return rc2;
+    SPAI_CUDA(cudaMemcpyAsync(blob.p, tb.f.data(), tb.f.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    const size_t smem = (size_t)(2 * tc::kM * tc::kKmax + tb.p.blob_floats) * sizeof(float);
+    SPAI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<tgrid, kTcThreads, smem, s>>>(args..., blob.as<float>(), tb.p, tcerr.as<int>());
+    count_launch();
     SPAI_CUDA(cudaGetLastError());
+    // the blob must stay alive until the kernel ran
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    return SPAI_OK;
+  };
+  {
+    // x = E_n(v), then the node terms of layer 1's message
+    TcBlob tb;
+    tb.add(rows_of(En.W1, dn, 0, H), dn, std::vector<float>(En.b1, En.b1 + H));
+    tb.add(rows_of(En.W2, H, 0, H), H, std::vector<float>(En.b2, En.b2 + H));
+    if (L > 0) {
+      const MLPView& m0 = fm(0);
+      std::vector<const float*> r = rows_of(m0.W1, m0.fi, 0, H);
+      std::vector<const float*> r2 = rows_of(m0.W1, m0.fi, H, H);
+      r.insert(r.end(), r2.begin(), r2.end());
+      std::vector<float> bias(m0.b1, m0.b1 + H);
+      bias.resize(2 * H, 0.f);
+      tb.add(r, H, bias);
+    }
+    tb.p.d_node = dn;
+    tb.p.has_m = L > 0;
+    if ((rc = launch_tc(node_enc_tc_kernel, tb, encblob, node_feat, n, xbuf.as<float>(), pqm.as<float>()))) return rc;
   }
   EdgeArgs ea;
   memset(&ea, 0, sizeof(ea));
@@ -531,22 +705,36 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     SPAI_CUDA(cudaGetLastError());
   }
   for (int t = 0; t < L; ++t) {
-    NodeLayerParams np_;
-    memset(&np_, 0, sizeof(np_));
-    const MLPView& m = fm(t);
-    const MLPView& v = fv(t);
-    memcpy(np_.W2m, m.W2, sizeof(np_.W2m));
-    memcpy(np_.b2m, m.b2, sizeof(np_.b2m));
-    memcpy(np_.W1v, v.W1, sizeof(np_.W1v));
-    memcpy(np_.b1v, v.b1, sizeof(np_.b1v));
-    memcpy(np_.W2v, v.W2, sizeof(np_.W2v));
-    memcpy(np_.b2v, v.b2, sizeof(np_.b2v));
-    split(fe(t), np_.e);
-    np_.has_m = (t + 1 < L);
-    if (np_.has_m) split(fm(t + 1), np_.m);
-    node_layer_kernel<<<ngrid, nb, 0, s>>>(P->g_rp(), n, sbuf.as<float>(), xbuf.as<float>(), pqe.as<float>(),
-                                           pqm.as<float>(), np_); count_launch();
-    SPAI_CUDA(cudaGetLastError());
+    {
+      const MLPView& m = fm(t);
+      const MLPView& v = fv(t);
+      const MLPView& e = fe(t);
+      TcBlob tb;
+      tb.add(rows_of(m.W2, H, 0, H), H, std::vector<float>(m.b2, m.b2 + H));
+      tb.add(rows_of(v.W1, H, 0, H), H, std::vector<float>(v.b1, v.b1 + H));
+      tb.add(rows_of(v.W2, H, 0, H), H, std::vector<float>(v.b2, v.b2 + H));
+      std::vector<const float*> r = rows_of(e.W1, e.fi, 0, H);
+      std::vector<const float*> r2 = rows_of(e.W1, e.fi, H, H);
+      r.insert(r.end(), r2.begin(), r2.end());
+      std::vector<float> bias(e.b1, e.b1 + H);
+      bias.resize(2 * H, 0.f);
+      const bool has_m = (t + 1 < L);
+      if (has_m) {
+        const MLPView& mn = fm(t + 1);
+        std::vector<const float*> r3 = rows_of(mn.W1, mn.fi, 0, H);
+        std::vector<const float*> r4 = rows_of(mn.W1, mn.fi, H, H);
+        r.insert(r.end(), r3.begin(), r3.end());
+        r.insert(r.end(), r4.begin(), r4.end());
+        bias.insert(bias.end(), mn.b1, mn.b1 + H);
+        bias.resize(4 * H, 0.f);
+      }
+      tb.add(r, H, bias);
+      tb.p.has_m = has_m;
+      DevMem lblob;
+      if ((rc = launch_tc(node_layer_tc_kernel, tb, lblob, P->g_rp(), n, (const float*)sbuf.as<float>(),
+                          xbuf.as<float>(), pqe.as<float>(), pqm.as<float>())))
+        return rc;
+    }
     EdgeParams p;
     memset(&p, 0, sizeof(p));
     const MLPView& e = fe(t);
@@ -564,8 +752,11 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     SPAI_CUDA(cudaGetLastError());
   }
   double hn = 0.0;
+  int herr = 0;
   SPAI_CUDA(cudaMemcpyAsync(&hn, normb.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SPAI_CUDA(cudaMemcpyAsync(&herr, tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   SPAI_CUDA(cudaStreamSynchronize(s));
+  if (herr) return set_error(SPAI_ERR_TIMEOUT, "gnn: a tensor-core wait timed out");
   Pre->anorm = hn;
   out = Pre;
   return SPAI_OK;
