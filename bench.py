@@ -382,6 +382,32 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# profiling case: one short solve (for ncu captures of single launches)
+# ---------------------------------------------------------------------------
+def run_probe(args):
+    """Builds the workload at --grid, runs the GNN forward once and one mixed
+    solve capped at --probe-iters iterations (rtol 0), no timing.  Small
+    enough for an ncu capture of one engine launch."""
+    import torch
+
+    import paper_2510_27517_gb300 as spai
+
+    torch.cuda.set_device(0)
+    h = make_host_workload(args, 0)
+    A_h = h["A"]
+    A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
+    P = spai.build_pattern(A, spai.PATTERN_FULL)
+    M = spai.gnn_precond(A, P, torch.tensor(h["v"], device="cuda"), torch.tensor(h["blob"], device="cuda"), d_node=4,
+                         n_layers=4, g_dtype=spai.F32, eps=args.eps)
+    x = torch.zeros(A_h.n, dtype=torch.float64, device="cuda")
+    r = spai.pcg_solve(A, M, torch.tensor(h["b"], device="cuda"), x, precision=spai.PREC_MIXED, rtol=0.0,
+                       max_iter=args.probe_iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": True, "n": A_h.n, "nnz": A_h.nnz, "iters": r["iters"], "engine_ms": r["engine_ms"],
+                      "slots": r["slots"]}))
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the float64 CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args):
@@ -429,12 +455,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic-per-iter", type=float, default=0.0,
                     help="DRAM bytes per inner iteration from an ncu capture of the current kernel")
+    ap.add_argument("--probe", action="store_true", help="one short solve for profiler captures")
+    ap.add_argument("--probe-iters", type=int, default=30)
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-k", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=6, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_leg:
         cpu_leg(args)
+    elif args.probe:
+        run_probe(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
