@@ -69,15 +69,20 @@ def matrix_norm(aval: np.ndarray) -> float:
 
 def gnn_forward(n: int, rowptr: np.ndarray, colidx: np.ndarray, aval: np.ndarray,
                 node_feat: np.ndarray, blob: np.ndarray, n_layers: int = 4,
-                msg_raw_edge: bool = False, return_latents: bool = False):
-    """Values of G on A's pattern (one per stored entry, CSR order)."""
+                msg_raw_edge: bool = False, return_latents: bool = False, a_norm: float | None = None):
+    """Values of G on A's pattern (one per stored entry, CSR order).
+
+    ``a_norm`` is ||A|| (Sec. 3.3) when the given rows are a sub-block of a
+    larger matrix whose own norm must scale the edge features; by default
+    it is computed from ``aval``."""
     node_feat = np.asarray(node_feat, dtype=np.float64).reshape(n, -1)
     d_node = node_feat.shape[1]
     params = unpack(blob, d_node, n_layers, msg_raw_edge)
     E_n, E_e, D = params[0], params[1], params[-1]
     rows = np.repeat(np.arange(n), np.diff(rowptr.astype(np.int64)))
     cols = colidx.astype(np.int64)
-    e = (np.asarray(aval, dtype=np.float64) / matrix_norm(aval)).reshape(-1, 1)
+    nrm = matrix_norm(aval) if a_norm is None else float(a_norm)
+    e = (np.asarray(aval, dtype=np.float64) / nrm).reshape(-1, 1)
 
     x = mlp(E_n, node_feat)
     h = mlp(E_e, e)

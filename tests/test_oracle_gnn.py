@@ -94,3 +94,30 @@ def test_message_uses_sum_over_neighbours():
     _, x, _ = gnn.gnn_forward(3, np.array(fx["rowptr"]), np.array(fx["colidx"]), np.array(fx["aval"]),
                               np.array(fx["node_feat"]), blob, n_layers=1, return_latents=True)
     assert np.allclose(x[:, 0], [4.85, 9.5, 9.85], rtol=1e-12)
+
+
+@pytest.mark.parametrize("L", [1, 4])
+def test_locality_ball_reproduces_full_forward(L):
+    """Eq. 4 propagates information one hop per layer, so the forward pass
+    on the (L + 1)-hop ball around a row (edge features scaled by the whole
+    matrix's norm) gives that row's values of G exactly.  This is what the
+    full-size GPU checks rely on; a radius of L hops must not suffice."""
+    from tests.ball import ball, entries_of_rows, submatrix
+    A, k = W.diffusion3d(12)
+    v = W.diffusion3d_node_features(k)
+    blob = W.gnn_random_weights(4, L)
+    full = gnn.gnn_forward(A.n, A.rowptr, A.colidx, A.val, v, blob, n_layers=L)
+    seeds = np.array([0, 6 * 144 + 6 * 12 + 6, A.n - 1])
+    nrm = gnn.matrix_norm(A.val)
+    for radius, exact in ((L + 1, True), (L, False)):
+        nodes = ball(A, seeds, radius)
+        sub, ent = submatrix(A, nodes)
+        g = gnn.gnn_forward(sub.n, sub.rowptr, sub.colidx, sub.val, v[nodes], blob, n_layers=L, a_norm=nrm)
+        loc = np.searchsorted(nodes, seeds)
+        mine = entries_of_rows(sub, loc)
+        want = full[ent[mine]]
+        err = np.abs(g[mine] - want).max() / np.abs(full).max()
+        if exact:
+            assert err <= 1e-13, err
+        else:
+            assert err > 1e-9, err
