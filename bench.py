@@ -382,6 +382,308 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# further workloads (not the headline line): graph Laplacian, uneven batch,
+# continuous-batching serving
+# ---------------------------------------------------------------------------
+def _common_line(args, metric, value, unit, config, extra, higher=True, dtype="f32"):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": higher, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic (seeded generators; random-init GNN weights)", "config": config}
+    line.update(extra)
+    return line
+
+
+def _peak_hbm():
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    return peaks.get("hbm_gbs", FALLBACK_HBM_GBS), ("measured" if peaks else "fallback")
+
+
+def _gnn_for(spai, A_dev, A_h, feat, blob, d_node, gdt, eps):
+    import torch
+    P = spai.build_pattern(A_dev, spai.PATTERN_FULL)
+    M = spai.gnn_precond(A_dev, P, torch.tensor(feat, device="cuda").reshape(A_h.n, d_node).contiguous(),
+                         torch.tensor(blob, device="cuda"), d_node=d_node, n_layers=4, g_dtype=gdt, eps=eps)
+    return P, M
+
+
+def _timed(fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def run_graph(args):
+    """Weighted graph Laplacian, n = 10^6, 8 * 10^6 random edges (weights
+    log-uniform in [1e-3, 1], shift 1e-4 * mean diagonal), b ~ N(0, 1):
+    mixed (float32 PCG in float64 refinement) against plain float64 PCG, both
+    to rtol 1e-8 with the GNN-built G (row-average node feature)."""
+    import numpy as np
+    import torch
+
+    import paper_2510_27517_gb300 as spai
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    A_h = W.graph_laplacian(args.graph_n, 8 * args.graph_n)
+    feat = W.row_average_feature(A_h).astype(np.float32)
+    blob = W.gnn_random_weights(1, 4, seed=W.BASE_SEED + 100)
+    b = torch.tensor(W.rhs_normal(A_h.n, W.BASE_SEED + 30), device="cuda")
+    A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
+    S = spai.system_create(A)
+    forms = {}
+    for name, prec, gdt in (("mixed", spai.PREC_MIXED, spai.F32), ("f64", spai.PREC_F64, spai.F64)):
+        P, M = _gnn_for(spai, A, A_h, feat, blob, 1, gdt, args.eps)
+        x = torch.zeros(A_h.n, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            x.zero_()
+            spai.system_solve(S, M, b, x, precision=prec, rtol=1e-8, max_iter=args.max_iter)
+        ts, res = [], None
+        for _ in range(args.steps):
+            x.zero_()
+            res, ms = _timed(lambda: spai.system_solve(S, M, b, x, precision=prec, rtol=1e-8, max_iter=args.max_iter))
+            ts.append(ms)
+        s_v, s_g = (4, 4) if prec == spai.PREC_MIXED else (8, 8)
+        b_it, b_out = algorithmic_bytes(A_h.n, A_h.nnz, A_h.nnz, s_v, s_g)
+        if prec == spai.PREC_F64:
+            b_out = 0
+        gbs = (res["iters"] * b_it + (res["outer_iters"] + 1) * b_out) / (res["engine_ms"] / 1e3) / 1e9
+        forms[name] = {"ms_per_solve": statistics.median(ts), "iters": res["iters"], "outer_iters": res["outer_iters"],
+                       "true_rel_res": res["true_rel_res"], "engine_gbs": gbs, "x": x.clone()}
+        M.close(), P.close()
+    d = (forms["mixed"]["x"] - forms["f64"]["x"]).norm().item() / forms["f64"]["x"].norm().item()
+    for f in forms.values():
+        f.pop("x")
+    peak, src = _peak_hbm()
+    for f in forms.values():
+        f["engine_frac_of_" + src] = f["engine_gbs"] / peak
+    line = _common_line(args, "solves/s to rtol 1e-8 (graph Laplacian, mixed vs float64)",
+                        1e3 / forms["mixed"]["ms_per_solve"], "solves/s",
+                        {"workload": f"graph Laplacian n={A_h.n} nnz={A_h.nnz}, GNN-SPAI G, eps {args.eps}"},
+                        {"mixed": forms["mixed"], "f64": forms["f64"], "speedup_mixed_vs_f64":
+                         forms["f64"]["ms_per_solve"] / forms["mixed"]["ms_per_solve"],
+                         "rel_x_diff_mixed_vs_f64": d, "hbm_peak_gbs": peak})
+    print(json.dumps(line))
+
+
+def run_batch(args):
+    """A batch of uneven 2D anisotropic systems (sides log-uniform in
+    [32, 512], anisotropy log-uniform in [1, 1e3], angle uniform), GNN-built
+    G per system, all solved together in persistent launches to rtol 1e-8
+    (float32 PCG in float64 refinement); against the same systems solved one
+    after another."""
+    import numpy as np
+    import torch
+
+    import paper_2510_27517_gb300 as spai
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    specs = W.aniso2d_batch(args.batch, side_lo=32, side_hi=args.batch_side_hi)
+    blob = W.gnn_random_weights(1, 4, seed=W.BASE_SEED + 100)
+    systems, preconds, bs, keep = [], [], [], []
+    sum_n = sum_nnz = 0
+    sizes = []
+    for i, (N, a, th) in enumerate(specs):
+        A_h = W.aniso2d(N, a, th)
+        A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
+        P, M = _gnn_for(spai, A, A_h, W.row_average_feature(A_h).astype(np.float32), blob, 1, spai.F32, args.eps)
+        S = spai.system_create(A, autotune=args.autotune)
+        systems.append(S), preconds.append(M), keep.append((A, P))
+        bs.append(torch.tensor(W.rhs_uniform(A_h.n, W.BASE_SEED + 1000 + i), device="cuda"))
+        sum_n += A_h.n
+        sum_nnz += A_h.nnz
+        sizes.append((A_h.n, A_h.nnz))
+    xs = [torch.zeros_like(b) for b in bs]
+    kw = dict(precision=spai.PREC_MIXED, rtol=1e-8, max_iter=args.max_iter)
+
+    def batch():
+        for x in xs:
+            x.zero_()
+        return spai.pcg_solve_batched(systems, preconds, bs, xs, **kw)
+
+    for _ in range(args.warmup):
+        batch()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = spai.kernel_launches()
+    ts, res = [], None
+    for _ in range(args.steps):
+        res, ms = _timed(batch)
+        ts.append(ms)
+    launches = (spai.kernel_launches() - l0) / args.steps
+    clk = clocks.stop()
+    bad = [i for i, r in enumerate(res) if r["status"] != 0 or not r["true_rel_res"] <= 1e-8]
+    if bad:
+        raise RuntimeError(f"{len(bad)} systems missed rtol 1e-8: {[res[i] for i in bad[:3]]}")
+    eng_ms = max(r["engine_ms"] for r in res)
+    tot_bytes = 0
+    for (n, nnz), r in zip(sizes, res):
+        b_it, b_out = algorithmic_bytes(n, nnz, nnz, 4, 4)
+        tot_bytes += r["iters"] * b_it + (r["outer_iters"] + 1) * b_out
+    gbs = tot_bytes / (eng_ms / 1e3) / 1e9
+    ms = statistics.median(ts)
+    alone_ms = None
+    if not args.no_alone:
+        def seq():
+            out = []
+            for S, M, b, x in zip(systems, preconds, bs, xs):
+                x.zero_()
+                out.append(spai.system_solve(S, M, b, x, **kw))
+            return out
+        _, alone_ms = _timed(seq)
+    peak, src = _peak_hbm()
+    iters = [r["iters"] for r in res]
+    line = _common_line(args, "solves/s to rtol 1e-8 (batch of uneven anisotropic systems)", args.batch / (ms / 1e3),
+                        "solves/s",
+                        {"workload": f"{args.batch} anisotropic 2D systems, sides log-uniform [32, {args.batch_side_hi}], "
+                                     f"GNN-SPAI G (f32), eps {args.eps}, f32 PCG in f64 refinement",
+                         "sum_n": sum_n, "sum_nnz": sum_nnz, "autotune": bool(args.autotune)},
+                        {"ms_per_batch": ms, "engine_ms": eng_ms, "iters_min": min(iters), "iters_max": max(iters),
+                         "iters_mean": statistics.mean(iters),
+                         "aggregate": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                       "frac": gbs / peak, "peak_source": src},
+                         "one_at_a_time_ms": alone_ms,
+                         "batch_speedup": (alone_ms / ms) if alone_ms else None,
+                         "gpu_launches": launches, "clocks": clk})
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """Continuous-batching serving against the plain float64 one-at-a-time
+    form on the same request trace.
+
+    Pool: 48 device-resident systems, 16 from each generator (2D Poisson,
+    3D diffusion, graph Laplacian), n log-uniform in [serve_n_lo,
+    serve_n_hi], each with a GNN-built G (float32 for the server, float64
+    for the baseline).  Trace: R requests, each a uniformly drawn system with
+    its own b (seeded by the request id), Poisson arrivals at rate
+    c * mu64 for every c of --rates, mu64 the measured float64
+    one-at-a-time throughput.  The baseline's latencies at each rate follow
+    from its measured per-request service times (first come, first served)."""
+    import numpy as np
+    import torch
+
+    import paper_2510_27517_gb300 as spai
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    g = np.random.default_rng(W.BASE_SEED + 5)
+    blob1 = W.gnn_random_weights(1, 4, seed=W.BASE_SEED + 100)
+    blob4 = W.gnn_random_weights(4, 4, seed=W.BASE_SEED + 100)
+    pool = []
+    lo, hi = math.log(args.serve_n_lo), math.log(args.serve_n_hi)
+    for gen in ("poisson2d", "diffusion3d", "graph"):
+        for j in range(16):
+            n_t = math.exp(g.uniform(lo, hi))
+            if gen == "poisson2d":
+                A_h = W.poisson2d(max(8, int(round(math.sqrt(n_t)))))
+                feat, d_node, blob = W.row_average_feature(A_h), 1, blob1
+            elif gen == "diffusion3d":
+                A_h, k = W.diffusion3d(max(8, int(round(n_t ** (1 / 3)))), 1.5, 8.0, seed=W.BASE_SEED + 200 + j)
+                feat, d_node, blob = W.diffusion3d_node_features(k), 4, blob4
+            else:
+                nn = int(round(n_t))
+                A_h = W.graph_laplacian(nn, 8 * nn, seed=W.BASE_SEED + 300 + j)
+                feat, d_node, blob = W.row_average_feature(A_h), 1, blob1
+            A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
+            P32, M32 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, spai.F32, args.eps)
+            P64, M64 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, spai.F64, args.eps)
+            S = spai.system_create(A)
+            pool.append({"gen": gen, "n": A_h.n, "nnz": A_h.nnz, "A": A, "S": S, "M32": M32, "M64": M64,
+                         "keep": (P32, P64)})
+    R = args.requests
+    sys_of = g.integers(0, len(pool), size=R)
+    b_host = [torch.from_numpy(W.rhs_uniform(pool[s]["n"], W.BASE_SEED + 10_000 + i)).pin_memory()
+              for i, s in enumerate(sys_of)]
+    x_host = [torch.empty_like(b).pin_memory() for b in b_host]
+
+    # float64 one-at-a-time: H2D b, solve on the device-resident system, D2H x
+    def one(i, prec=spai.PREC_F64):
+        p = pool[sys_of[i]]
+        bd = b_host[i].to("cuda", non_blocking=True)
+        xd = torch.zeros_like(bd)
+        r = spai.system_solve(p["S"], p["M64"] if prec == spai.PREC_F64 else p["M32"], bd, xd, precision=prec,
+                              rtol=1e-8, max_iter=args.max_iter)
+        x_host[i].copy_(xd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return r
+
+    for i in range(min(3, R)):
+        one(i)
+    svc = []
+    t0 = time.perf_counter()
+    for i in range(R):
+        t = time.perf_counter()
+        r = one(i)
+        if r["status"] != 0 or not r["true_rel_res"] <= 1e-8:
+            raise RuntimeError(f"float64 solve {i} missed rtol: {r}")
+        svc.append(time.perf_counter() - t)
+    t64 = time.perf_counter() - t0
+    mu64 = R / t64
+
+    def fifo(arr):
+        done, lat = 0.0, []
+        for a, s in zip(arr, svc):
+            st = max(a, done)
+            done = st + s
+            lat.append(done - a)
+        return lat, done
+
+    srv = spai.Server(hbm_cap_bytes=args.hbm_cap_gb << 30, max_slots=args.max_slots, chunk_iters=args.chunk_iters,
+                      precision=spai.PREC_MIXED, rtol=1e-8, max_iter=args.max_iter)
+    ids = [srv.register(p["S"], p["M32"]) for p in pool]
+    # warm the server
+    for i in range(min(3, R)):
+        srv.wait(srv.submit(ids[sys_of[i]], b_host[i], x_host[i]), timeout_ms=600000)
+    rates = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for c in [float(v) for v in args.rates.split(",")]:
+        lam = c * mu64
+        gaps = g.exponential(1.0 / lam, size=R)
+        arr = np.cumsum(gaps) - gaps[0]
+        tickets = []
+        start = time.perf_counter()
+        for i in range(R):
+            now = time.perf_counter() - start
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            tickets.append(srv.submit(ids[sys_of[i]], b_host[i], x_host[i]))
+        comps = [srv.wait(t, timeout_ms=3_600_000) for t in tickets]
+        bad = [cp for cp in comps if cp["status"] != 0 or not cp["true_rel_res"] <= 1e-8]
+        if bad:
+            raise RuntimeError(f"served solve missed rtol: {bad[:3]}")
+        lat = np.array([(cp["t_done_us"] - cp["t_submit_us"]) / 1e6 for cp in comps])
+        span = (max(cp["t_done_us"] for cp in comps) - min(cp["t_submit_us"] for cp in comps)) / 1e6
+        lat64, done64 = fifo(arr)
+        rates.append({"rate_x_mu64": c, "arrivals_per_s": lam,
+                      "served": {"solves_per_s": R / span, "p50_s": float(np.percentile(lat, 50)),
+                                 "p99_s": float(np.percentile(lat, 99))},
+                      "f64_one_at_a_time": {"solves_per_s": R / done64,
+                                            "p50_s": float(np.percentile(lat64, 50)),
+                                            "p99_s": float(np.percentile(lat64, 99))}})
+    clk = clocks.stop()
+    srv.close()
+    top = max(rates, key=lambda r: r["served"]["solves_per_s"])
+    line = _common_line(args, "serving solves/s to rtol 1e-8 (continuous batching vs float64 one-at-a-time)",
+                        top["served"]["solves_per_s"], "solves/s",
+                        {"workload": f"{R} requests over 48 systems (Poisson 2D, diffusion 3D, graph Laplacian), "
+                                     f"n log-uniform [{args.serve_n_lo}, {args.serve_n_hi}], Poisson arrivals",
+                         "hbm_cap_gb": args.hbm_cap_gb, "max_slots": args.max_slots, "chunk_iters": args.chunk_iters,
+                         "eps": args.eps},
+                        {"mu64_solves_per_s": mu64, "ratio_vs_f64_one_at_a_time": top["served"]["solves_per_s"] / mu64,
+                         "rates": rates, "clocks": clk,
+                         "pool": {gen: sorted(p["n"] for p in pool if p["gen"] == gen)
+                                  for gen in ("poisson2d", "diffusion3d", "graph")}})
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
 # profiling case: one short solve (for ncu captures of single launches)
 # ---------------------------------------------------------------------------
 def run_probe(args):
@@ -455,6 +757,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic-per-iter", type=float, default=0.0,
                     help="DRAM bytes per inner iteration from an ncu capture of the current kernel")
+    ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "graph", "batch", "serve"])
+    ap.add_argument("--graph-n", type=int, default=1_000_000)
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--batch-side-hi", type=int, default=512)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-alone", action="store_true")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rates", default="0.5,1,2,4,8")
+    ap.add_argument("--serve-n-lo", type=int, default=10_000)
+    ap.add_argument("--serve-n-hi", type=int, default=262_144)
+    ap.add_argument("--hbm-cap-gb", type=int, default=120)
+    ap.add_argument("--max-slots", type=int, default=64)
+    ap.add_argument("--chunk-iters", type=int, default=16)
     ap.add_argument("--probe", action="store_true", help="one short solve for profiler captures")
     ap.add_argument("--probe-iters", type=int, default=30)
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
@@ -467,6 +782,12 @@ def main():
         run_probe(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "graph":
+        run_graph(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
