@@ -197,13 +197,43 @@ void spai_precond_destroy(spai_precond* M);
 
 /* ------------------------------------------------------------------------ *
  * Systems: A prepared for repeated solves (validated, float32 copy, SpMV
- * schedule).  `autotune` nonzero times candidate schedules on the device and
- * keeps the fastest; the choice depends only on A, never on what else runs.
+ * schedule).  The schedule of the persistent solver's three sparse passes
+ * (A, G^T, G; the paper runs library SpMVs and has no counterpart) is:
+ *   tile_nnz    entries per row group (rows binned by their first entry),
+ *   items_log2  groups per work item = heuristic count * 2^items_log2,
+ *   staged      1: groups staged into shared memory by TMA bulk copies
+ *               (rows of at most 1024 entries), 0: direct loads,
+ *   sell        1: matrices with a SELL-32 copy (slices of 32 rows stored
+ *               column-major; built when rows have at most 64 entries and
+ *               padding adds at most 25%) are read in that layout, one row
+ *               per lane; 0: CSR row groups.  The group size of the SELL
+ *               layout scales with tile_nnz.
+ * Per-row sums are the same in every schedule (entries in stored order);
+ * dot products are summed in a schedule-dependent fixed order.
+ * The default is the heuristic schedule (sell 1).  `autotune` nonzero makes
+ * the first solve of the system (spai_system_solve or spai_pcg_solve_batched)
+ * time short runs of every candidate (tile_nnz T0, T0/2, T0/4; items_log2
+ * -1, 0, 1; SELL, CSR staged, CSR direct) with that solve's preconditioner
+ * and precision and keep the fastest; it is then fixed, so a system's
+ * results are the same alone and in any batch.
  * ------------------------------------------------------------------------ */
 int spai_system_create(const spai_csr* A, int32_t autotune, spai_system** out, void* stream);
 
-/* Schedule chosen for the system: tile size in nonzeros and block size. */
-int spai_system_schedule(const spai_system* S, int32_t* tile_nnz, int32_t* block_threads);
+typedef struct {
+  int32_t tile_nnz;    /* entries per row group (CSR) ; 0 in set: the default */
+  int32_t items_log2;  /* -4..4 */
+  int32_t staged;      /* 0 or 1 */
+  int32_t sell;        /* 1: SELL-32 layout for the matrices that have one, 0: CSR row groups */
+  int32_t tuned;       /* out: 1 once the autotuner ran or a schedule was set */
+} spai_schedule;
+
+/* The system's schedule. */
+int spai_system_schedule(const spai_system* S, spai_schedule* out);
+
+/* Fixes the schedule (no autotuning afterwards).  SPAI_ERR_INVALID for a
+ * field out of range (tile_nnz above the largest group that fits the
+ * staging buffer for this matrix, items_log2 outside -4..4, flags not 0/1). */
+int spai_system_set_schedule(spai_system* S, const spai_schedule* sch);
 
 void spai_system_destroy(spai_system* S);
 
@@ -223,12 +253,15 @@ int spai_pcg_solve(const spai_csr* A, const spai_precond* M, const double* b, do
 int spai_system_solve(spai_system* S, const spai_precond* M, const double* b, double* x,
                       const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);
 
-/* Many systems in one persistent launch: systems advance in lockstep, each
- * with its own scalars, and leave the work list when they converge.  Arrays
- * have nsys entries; res[i] is filled for every system; the return value is
- * SPAI_OK if every system converged, else the first failing status.  One
- * system's failure does not stop the others.  All systems use the same
- * opts (history recording is ignored). */
+/* Many uneven systems solved together (the batching form; the paper solves
+ * one system at a time): systems advance in lockstep in a persistent kernel,
+ * each with its own scalars, and leave the work list when they converge.  The
+ * whole solve is one CUDA graph launch -- a device-side while loop over
+ * persistent launches -- so no host round trip happens until every system is
+ * done.  Arrays have nsys entries; res[i] is filled for every system; the
+ * return value is SPAI_OK if every system converged, else the first failing
+ * status.  One system's failure does not stop the others.  All systems use
+ * the same opts (history recording is ignored) and the same G storage type. */
 int spai_pcg_solve_batched(int32_t nsys, spai_system* const* S, const spai_precond* const* M,
                            const double* const* b, double* const* x, const spai_pcg_opts* opts,
                            spai_pcg_result* res, void* stream);

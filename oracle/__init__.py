@@ -16,8 +16,10 @@ Contents (each function cites the passage of the paper it follows):
   Eqs. 3-5) with the dimension-agnostic norm of Sec. 3.3.
 * ``pcg``      - CSR mat-vec, the preconditioner apply of Eq. 2 and
   Algorithm 1 (App. A) with residual replacement.
+* ``spectrum`` - kappa and Kaporin's condition number of M^-1 A (Sec. 4.5),
+  dense, and the Ritz values of the CG / Lanczos tridiagonal matrix.
 
 All arithmetic is float64 (the paper fixes no precision).  The code is written
 for readability, not speed: plain numpy with no blocking or fusion.
 """
-from . import pattern, fsai, gnn, pcg  # noqa: F401
+from . import pattern, fsai, gnn, pcg, spectrum  # noqa: F401

@@ -12,7 +12,8 @@ namespace spai {
 
 int engine_tile_nnz(int32_t max_row);
 int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const double* const* b, double* const* x,
-               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override);
+               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override, int use_graph);
+int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s);
 
 static thread_local std::string g_err = "no error";
 static std::atomic<uint64_t> g_launches{0};
@@ -162,6 +163,7 @@ int make_precond_from_values(const std::shared_ptr<PatternData>& P, const void* 
                                                          P->perm.as<int32_t>(), P->nnz); count_launch();
     SPAI_CUDA(cudaGetLastError());
   }
+  if ((rc = precond_sell(*M, s))) return rc;
   out = M;
   return SPAI_OK;
 }
@@ -233,9 +235,23 @@ int make_system(const spai_csr* A, int autotune, std::shared_ptr<SystemData>& ou
   S->colidx.keep();
   S->val64.keep();
   S->val32.keep();
-  S->block = 256;
   S->tile_nnz = engine_tile_nnz(S->max_row);
-  (void)autotune;
+  S->autotune = autotune ? 1 : 0;
+  if ((rc = build_sell(S->rowptr.as<int32_t>(), S->colidx.as<int32_t>(), S->n, S->nnz, S->max_row, S->sell_a, s)))
+    return rc;
+  if (S->sell_a.nslices > 0) {
+    const size_t tot = (size_t)S->sell_a.total + 64;
+    if ((rc = S->sell_v64.alloc(tot * sizeof(double), s))) return rc;
+    if ((rc = S->sell_v32.alloc(tot * sizeof(float), s))) return rc;
+    SPAI_CUDA(cudaMemsetAsync(S->sell_v64.p, 0, tot * sizeof(double), s));
+    SPAI_CUDA(cudaMemsetAsync(S->sell_v32.p, 0, tot * sizeof(float), s));
+    if ((rc = sell_values(S->sell_a, S->rowptr.as<int32_t>(), S->n, S->val64.p, SPAI_F64, S->sell_v64.p, SPAI_F64, s)))
+      return rc;
+    if ((rc = sell_values(S->sell_a, S->rowptr.as<int32_t>(), S->n, S->val64.p, SPAI_F64, S->sell_v32.p, SPAI_F32, s)))
+      return rc;
+    S->sell_v64.keep();
+    S->sell_v32.keep();
+  }
   out = S;
   return SPAI_OK;
 }
@@ -252,12 +268,44 @@ extern "C" int spai_system_create(const spai_csr* A, int32_t autotune, spai_syst
   return SPAI_OK;
 }
 
-extern "C" int spai_system_schedule(const spai_system* S, int32_t* tile_nnz, int32_t* block_threads) {
-  if (!S) return set_error(SPAI_ERR_INVALID, "null system");
-  if (tile_nnz) *tile_nnz = S->d->tile_nnz;
-  if (block_threads) *block_threads = S->d->block;
+extern "C" int spai_system_schedule(const spai_system* S, spai_schedule* out) {
+  if (!S || !out) return set_error(SPAI_ERR_INVALID, "null argument");
+  out->tile_nnz = S->d->tile_nnz;
+  out->items_log2 = S->d->items_log2;
+  out->staged = S->d->staged;
+  out->sell = S->d->sell;
+  out->tuned = S->d->tuned;
   return SPAI_OK;
 }
+
+extern "C" int spai_system_set_schedule(spai_system* S, const spai_schedule* sch) {
+  if (!S || !sch) return set_error(SPAI_ERR_INVALID, "null argument");
+  SystemData& d = *S->d;
+  const int32_t t0 = engine_tile_nnz(d.max_row);
+  if (sch->tile_nnz < 0 || sch->tile_nnz > t0)
+    return set_error(SPAI_ERR_INVALID, "tile_nnz must be in 1..%d (0: default)", (int)t0);
+  if (sch->items_log2 < -4 || sch->items_log2 > 4) return set_error(SPAI_ERR_INVALID, "items_log2 must be in -4..4");
+  if ((sch->staged != 0 && sch->staged != 1) || (sch->sell != 0 && sch->sell != 1))
+    return set_error(SPAI_ERR_INVALID, "staged and sell must be 0 or 1");
+  d.tile_nnz = sch->tile_nnz ? sch->tile_nnz : t0;
+  d.items_log2 = sch->items_log2;
+  d.staged = sch->staged;
+  d.sell = sch->sell;
+  d.tuned = 1;
+  return SPAI_OK;
+}
+
+namespace {
+// Tunes (once) every system created with autotune that has not been tuned yet.
+int tune_pending(int nsys, SystemData* const* S, PrecondData* const* M, const spai_pcg_opts* o, cudaStream_t s) {
+  for (int i = 0; i < nsys; ++i) {
+    if (!S[i]->autotune || S[i]->tuned) continue;
+    int rc = engine_tune(S[i], M[i], o->precision == SPAI_PREC_MIXED, s);
+    if (rc) return rc;
+  }
+  return SPAI_OK;
+}
+}  // namespace
 
 extern "C" void spai_system_destroy(spai_system* S) { delete S; }
 
@@ -266,7 +314,10 @@ extern "C" int spai_system_solve(spai_system* S, const spai_precond* M, const do
   if (!S || !M || !b || !x || !opts || !res) return set_error(SPAI_ERR_INVALID, "null argument");
   SystemData* sp = S->d.get();
   PrecondData* mp = M->d.get();
-  return engine_run(1, &sp, &mp, &b, &x, opts, res, (cudaStream_t)stream, 0);
+  if (mp->P->n != sp->n) return set_error(SPAI_ERR_SHAPE, "G and A sizes differ");
+  int rc = tune_pending(1, &sp, &mp, opts, (cudaStream_t)stream);
+  if (rc) return rc;
+  return engine_run(1, &sp, &mp, &b, &x, opts, res, (cudaStream_t)stream, 0, 0);
 }
 
 extern "C" int spai_pcg_solve(const spai_csr* A, const spai_precond* M, const double* b, double* x,
@@ -277,7 +328,7 @@ extern "C" int spai_pcg_solve(const spai_csr* A, const spai_precond* M, const do
   if (rc) return rc;
   SystemData* sp = S.get();
   PrecondData* mp = M->d.get();
-  rc = engine_run(1, &sp, &mp, &b, &x, opts, res, (cudaStream_t)stream, 0);
+  rc = engine_run(1, &sp, &mp, &b, &x, opts, res, (cudaStream_t)stream, 0, 0);
   cudaStreamSynchronize((cudaStream_t)stream);
   return rc;
 }
@@ -295,7 +346,11 @@ extern "C" int spai_pcg_solve_batched(int32_t nsys, spai_system* const* S, const
   }
   spai_pcg_opts o = *opts;
   o.record_history = 0;
-  return engine_run(nsys, sp.data(), mp.data(), b, x, &o, res, (cudaStream_t)stream, 0);
+  for (int i = 0; i < nsys; ++i)
+    if (mp[i]->P->n != sp[i]->n) return set_error(SPAI_ERR_SHAPE, "G and A sizes differ (system %d)", i);
+  int rc = tune_pending(nsys, sp.data(), mp.data(), &o, (cudaStream_t)stream);
+  if (rc) return rc;
+  return engine_run(nsys, sp.data(), mp.data(), b, x, &o, res, (cudaStream_t)stream, 0, 1);
 }
 
 extern "C" int spai_pcg_solve_host(const spai_csr* A, const spai_precond* M, const double* b_host, double* x_host,

@@ -60,6 +60,9 @@ struct EngSys {
   int32_t ntiles[3];        // groups per matrix
   int32_t kgroups[3];       // groups per work item per matrix
   int32_t fits[3];          // every group fits the stage buffer
+  int32_t fmt[3];           // 0: CSR row groups (tiles = rows), 1: SELL-32 (tiles = slices)
+  const int32_t* sptr[3];   // SELL-32 slice offsets (fmt 1)
+  const int32_t* a_ci64;    // CSR column indices of A (float64 residual of mixed mode)
   int32_t nitems;           // work items of this system
   int32_t item_base;
   int32_t chunk_base;     // first chunk counter / chunk partial of this system
@@ -463,6 +466,90 @@ __device__ __forceinline__ void piped_groups(Pipe& P, const int32_t* __restrict_
   __syncthreads();
 }
 
+// SELL-32 groups [g0, g1) (a group = consecutive 32-row slices) through the
+// same stage ring: each slice is taken by one warp (slices dealt round-robin
+// over the warps, continuing across groups), lane l owns row 32 s + l, loads
+// its entries column-major from the staged slice (conflict-free), issues all
+// gathers of a batch of 8 entries before summing them, and sums its row in
+// stored order -- the same per-row arithmetic as the CSR path, without the
+// product buffer.
+template <int NS, class AT, class MV, class Op>
+__device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict__ tiles,
+                                             const int32_t* __restrict__ sptr, const int32_t* __restrict__ rp,
+                                             const int32_t* ci, const MV* val, int g0, int g1, int64_t n,
+                                             const Op& op, double& p0, double& p1, uint64_t limit_ns, int* err) {
+  const int ng = g1 - g0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kBlock / 32;
+  constexpr int kB = 8;
+  for (int i = threadIdx.x; i <= ng; i += blockDim.x) {
+    const int sl = __ldg(tiles + g0 + i);
+    P.grow[i] = sl;
+    P.gent[i] = __ldg(sptr + sl);
+  }
+  if (threadIdx.x < NS) P.rel[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t c0 = P.consumed;
+  if (threadIdx.x == 0) {
+    const int pre = ng < NS ? ng : NS;
+    for (int k = 0; k < pre; ++k) issue_group<MV>(P, ci, val, k, (int)((c0 + k) % NS));
+  }
+  uint32_t blocks = 0;
+  for (int k = 0; k < ng; ++k) {
+    const uint32_t c = c0 + k;
+    const int st = (int)(c % NS);
+    const unsigned parity = (c / NS) & 1u;
+    if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
+    const GroupHdr h = P.hdr[st];
+    const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+    const int32_t* cs = reinterpret_cast<const int32_t*>(base) - h.e0a;
+    const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) - h.e0a;
+    const int nsl = h.re - h.r;
+    int j = (int)((uint32_t)(warp - (int)(blocks % NW) + NW) % NW);
+    for (; j < nsl; j += NW) {
+      const int sl = h.r + j;
+      const int off = __ldg(sptr + sl);
+      const int w = (__ldg(sptr + sl + 1) - off) >> 5;
+      const int row = sl * 32 + lane;
+      const bool valid = row < n;
+      int len = 0;
+      typename Op::Pre pr;
+      if (valid) {
+        len = __ldg(rp + row + 1) - __ldg(rp + row);
+        pr = op.pre(row);
+      }
+      const int32_t* cl = cs + off + lane;
+      const MV* vl = vs + off + lane;
+      AT acc = AT(0);
+      for (int k0 = 0; k0 < w; k0 += kB) {
+        AT prod[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const int kk = k0 + u;
+          prod[u] = AT(0);
+          if (kk < len) prod[u] = rmul(Conv<AT>::f(vl[32 * kk]), op.gather(cl[32 * kk]));
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+          if (k0 + u < len) acc = radd(acc, prod[u]);
+      }
+      if (valid) op.fin(row, acc, pr, p0, p1);
+    }
+    blocks += (uint32_t)nsl;
+    if (lane == 0) {
+      __threadfence_block();
+      const int prev = atomicAdd(P.rel + st, 1);
+      if (prev == NW - 1) {
+        P.rel[st] = 0;
+        if (k + NS < ng) issue_group<MV>(P, ci, val, k + NS, st);
+      }
+    }
+    __syncwarp();
+  }
+  P.consumed = c0 + ng;
+  __syncthreads();
+}
+
 // Groups [g0, g1) without the stage ring (rows longer than a group, or the
 // float64 residual of mixed precision): direct loads.
 template <class AT, class MV, class Op>
@@ -478,8 +565,10 @@ template <class AT, class MV, class Op>
 __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* tiles, const int32_t* rp,
                                            const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
                                            double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
-                                           int* err) {
-  if (piped) piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0,
+                                           int* err, const int32_t* sptr = nullptr, int64_t n = 0) {
+  if (sptr) piped_slices<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, sptr, rp, ci, val, g0, g1, n,
+                                                                          op, p0, p1, limit_ns, err);
+  else if (piped) piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0,
                                                                               p1, limit_ns, err);
   else direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op, p0, p1);
 }
@@ -504,49 +593,60 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   const int m = phase_mat(ph);
   const int32_t* tl = S.tiles[m];
   const bool piped = S.fits[m] != 0;
+  const int32_t* sp = S.fmt[m] ? S.sptr[m] : nullptr;  // SELL-32 slices
+  const int64_t n = S.n;
 
   switch (ph) {
     case PH_P1: {
       OpP1<VT> op{s, d_cur, d_nxt, q, beta, st.first != 0};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_P2: {
       OpP2<VT> op{r_cur, r_nxt, q, d_cur, xv, t, alpha};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_APPLY1: {
       OpApply1<VT> op{r_cur, t};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_APPLY2: {
       OpApply2<VT> op{t, r_cur, s, eps};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+      run_groups<VT>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_RESID0:
     case PH_RESID: {
       if (!MIXED) {
         OpResid<VT> op{xv, S.b, r_cur};
-        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       } else {
         OpResidIn<VT> op{xv, rin, r_cur};
-        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err);
+        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       }
       break;
     }
     case PH_RESID64: {
       OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
-      direct_groups<double>(tl, S.rp[MAT_A], S.ci[MAT_A], S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red,
-                            op, p0, p1);
+      if (sp) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
+        uint32_t blocks = 0;
+        const int r0 = __ldg(tl + g0) * 32, r1 = (int)min((int64_t)__ldg(tl + g1) * 32, n);
+        if (r0 < r1)
+          spmv_rows<double>(S.rp[MAT_A], S.a_ci64, S.a_v64, r0, r1, reinterpret_cast<double*>(sbuf), red, op, p0,
+                            p1, blocks);
+      } else {
+        direct_groups<double>(tl, S.rp[MAT_A], S.a_ci64, S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red,
+                              op, p0, p1);
+      }
       break;
     }
     case PH_P2X:
     case PH_XUPD:
     case PH_ZEROX: {
-      const int r0 = __ldg(tl + g0), r1 = __ldg(tl + g1);
+      const int r0 = sp ? __ldg(tl + g0) * 32 : __ldg(tl + g0);
+      const int r1 = sp ? (int)min((int64_t)__ldg(tl + g1) * 32, n) : __ldg(tl + g1);
       for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
         if (ph == PH_P2X) xv[row] = radd(ldv(xv + row), rmul(alpha, ldv(d_cur + row)));
         else if (ph == PH_XUPD) {
@@ -825,6 +925,18 @@ __global__ void true_residual_kernel(const int32_t* __restrict__ rp, const int32
   }
 }
 
+// Body tail of the graph-resident solve loop: counts the persistent launch
+// that just ended and decides on the device whether another one runs.
+__global__ void engine_continue_kernel(GridSync* gs, int64_t slot_cap, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int live = *(volatile int*)&gs->live;
+    const int err = *(volatile int*)&gs->err;
+    const int slot = *(volatile int*)&gs->slot;
+    gs->pad[0] += 1;
+    cudaGraphSetConditional(h, (live > 0 && err == 0 && (int64_t)slot < slot_cap) ? 1u : 0u);
+  }
+}
+
 template <class VT, class GT, bool MIXED>
 const void* kernel_ptr() {
   return reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED>);
@@ -870,6 +982,17 @@ int engine_items_k(int ngroups, int grid) {
     if (items <= 1) break;
   }
   return best_k;
+}
+
+// The tuned multiple of the heuristic K (2^log2), kept within [1, min(ngroups, kMaxK)].
+int engine_scale_k(int k, int log2, int ngroups) {
+  int64_t v = k;
+  if (log2 > 0) v <<= (log2 > 8 ? 8 : log2);
+  if (log2 < 0) v >>= (-log2 > 8 ? 8 : -log2);
+  const int64_t hi = ngroups < kMaxK ? (ngroups > 0 ? ngroups : 1) : kMaxK;
+  if (v > hi) v = hi;
+  if (v < 1) v = 1;
+  return (int)v;
 }
 
 // Tile size for a matrix whose longest row has max_row entries: binning rows
@@ -943,36 +1066,71 @@ class EngineBatch {
       SystemData& A = *mb.S;
       PrecondData& P = *mb.M;
       const int tn = A.tile_nnz;
-      if ((rc = build_tiles(A.rowptr.as<int32_t>(), A.n, A.nnz, tn, A.tiles, s_))) return rc;
-      if ((rc = build_tiles(P.P->gt_rp(), P.P->n, P.P->nnz, tn, P.gt_tiles, s_))) return rc;
-      if ((rc = build_tiles(P.P->g_rp(), P.P->n, P.P->nnz, tn, P.g_tiles, s_))) return rc;
       EngSys& e = hs[i];
       memset(&e, 0, sizeof(e));
       e.rp[MAT_A] = A.rowptr.as<int32_t>();
-      e.ci[MAT_A] = A.colidx.as<int32_t>();
-      e.val[MAT_A] = mixed_ ? (const void*)A.val32.p : (const void*)A.val64.p;
+      e.a_ci64 = A.colidx.as<int32_t>();
       e.a_v64 = A.val64.as<double>();
       e.rp[MAT_GT] = P.P->gt_rp();
-      e.ci[MAT_GT] = P.P->gt_ci();
-      e.val[MAT_GT] = P.gt_val.p;
       e.rp[MAT_G] = P.P->g_rp();
-      e.ci[MAT_G] = P.P->g_ci();
-      e.val[MAT_G] = P.g_val.p;
+      const int fits = (engine_groups_fit(A.max_row) && A.staged) ? 1 : 0;
+      // SELL-32 where the matrix has the layout and the schedule asks for it
+      // (all three share one choice, so a system's arithmetic depends on its
+      // schedule only); the group size scales like the CSR one
+      const bool sell_a = A.sell && A.sell_a.nslices > 0 && A.sell_v64.p;
+      const bool sell_g = A.sell && P.P->sell.nslices > 0 && P.sell_g.p && P.sell_gt.p;
+      const int32_t t0 = engine_tile_nnz(A.max_row);
+      auto sell_tile = [&](int32_t width) {
+        const int64_t tmax = (int64_t)kCap + 1 - 32 * (int64_t)width;
+        int64_t t = tmax * tn / (t0 > 0 ? t0 : 1);
+        if (t > tmax) t = tmax;
+        return (int32_t)(t < 1 ? 1 : t);
+      };
+      if (sell_a) {
+        e.fmt[MAT_A] = 1;
+        e.sptr[MAT_A] = A.sell_a.sptr.as<int32_t>();
+        e.ci[MAT_A] = A.sell_a.ci.as<int32_t>();
+        e.val[MAT_A] = mixed_ ? (const void*)A.sell_v32.p : (const void*)A.sell_v64.p;
+        if ((rc = build_tiles(e.sptr[MAT_A], A.sell_a.nslices, A.sell_a.total, sell_tile(A.sell_a.max_width),
+                              A.tiles, s_)))
+          return rc;
+      } else {
+        e.ci[MAT_A] = A.colidx.as<int32_t>();
+        e.val[MAT_A] = mixed_ ? (const void*)A.val32.p : (const void*)A.val64.p;
+        if ((rc = build_tiles(A.rowptr.as<int32_t>(), A.n, A.nnz, tn, A.tiles, s_))) return rc;
+      }
+      if (sell_g) {
+        const SellData& L = P.P->sell;
+        const int32_t tg = sell_tile(L.max_width);
+        e.fmt[MAT_GT] = e.fmt[MAT_G] = 1;
+        e.sptr[MAT_GT] = e.sptr[MAT_G] = L.sptr.as<int32_t>();
+        e.ci[MAT_GT] = e.ci[MAT_G] = L.ci.as<int32_t>();
+        e.val[MAT_GT] = P.sell_gt.p;
+        e.val[MAT_G] = P.sell_g.p;
+        if ((rc = build_tiles(L.sptr.as<int32_t>(), L.nslices, L.total, tg, P.gt_tiles, s_))) return rc;
+        if ((rc = build_tiles(L.sptr.as<int32_t>(), L.nslices, L.total, tg, P.g_tiles, s_))) return rc;
+      } else {
+        e.ci[MAT_GT] = P.P->gt_ci();
+        e.val[MAT_GT] = P.gt_val.p;
+        e.ci[MAT_G] = P.P->g_ci();
+        e.val[MAT_G] = P.g_val.p;
+        if ((rc = build_tiles(P.P->gt_rp(), P.P->n, P.P->nnz, tn, P.gt_tiles, s_))) return rc;
+        if ((rc = build_tiles(P.P->g_rp(), P.P->n, P.P->nnz, tn, P.g_tiles, s_))) return rc;
+      }
       e.tiles[MAT_A] = A.tiles.starts.as<int32_t>();
       e.tiles[MAT_GT] = P.gt_tiles.starts.as<int32_t>();
       e.tiles[MAT_G] = P.g_tiles.starts.as<int32_t>();
       e.ntiles[MAT_A] = A.tiles.ntiles;
       e.ntiles[MAT_GT] = P.gt_tiles.ntiles;
       e.ntiles[MAT_G] = P.g_tiles.ntiles;
-      const int fits = engine_groups_fit(A.max_row) ? 1 : 0;
       int ng = 0;
       for (int mm = 0; mm < 3; ++mm) {
-        e.fits[mm] = fits;
+        e.fits[mm] = e.fmt[mm] ? 1 : fits;
         if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
       }
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
-      const int kg = engine_items_k(ng, grid_max_);
+      const int kg = engine_scale_k(engine_items_k(ng, grid_max_), A.items_log2, ng);
       e.nitems = (ng + kg - 1) / kg;
       for (int mm = 0; mm < 3; ++mm) e.kgroups[mm] = (e.ntiles[mm] + e.nitems - 1) / e.nitems;
       e.item_base = (int32_t)items;
@@ -1062,6 +1220,77 @@ class EngineBatch {
     if (grid_ > items) grid_ = (int)items;
     if (grid_ < 1) grid_ = 1;
     slots_ = 0;
+    return SPAI_OK;
+  }
+
+  // Runs every remaining phase from one CUDA graph: a while-conditional node
+  // whose body is the persistent launch (chunk slots) followed by a one-thread
+  // kernel that decides on the device whether another launch is needed, so the
+  // batch runs to the end without returning to the host.  Same kernel, same
+  // arguments and the same slot sequence as repeated launch() calls.
+  int run_graph(int chunk, int64_t slot_cap, cudaEvent_t ev0, cudaEvent_t ev1, double* ms, int* launches) {
+    *launches = 0;
+    if (live_ <= 0) return SPAI_OK;
+    args_.max_slots = chunk;
+    struct G {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t e = nullptr;
+      ~G() {
+        if (e) cudaGraphExecDestroy(e);
+        if (g) cudaGraphDestroy(g);
+      }
+    } gr;
+    SPAI_CUDA(cudaGraphCreate(&gr.g, 0));
+    cudaGraphConditionalHandle h;
+    SPAI_CUDA(cudaGraphConditionalHandleCreate(&h, gr.g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    SPAI_CUDA(cudaGraphAddNode(&loop, gr.g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    void* kargs[] = {&args_};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void*>(kfn_);
+    kp.gridDim = dim3(grid_);
+    kp.blockDim = dim3(kBlock);
+    kp.sharedMemBytes = (unsigned)smem_;
+    kp.kernelParams = kargs;
+    cudaGraphNode_t kn;
+    SPAI_CUDA(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
+    cudaKernelNodeAttrValue coop;
+    memset(&coop, 0, sizeof(coop));
+    coop.cooperative = 1;
+    SPAI_CUDA(cudaGraphKernelNodeSetAttribute(kn, cudaLaunchAttributeCooperative, &coop));
+    GridSync* gs = args_.gs;
+    void* cargs[] = {&gs, &slot_cap, &h};
+    cudaKernelNodeParams cpk;
+    memset(&cpk, 0, sizeof(cpk));
+    cpk.func = reinterpret_cast<void*>(&engine_continue_kernel);
+    cpk.gridDim = dim3(1);
+    cpk.blockDim = dim3(32);
+    cpk.kernelParams = cargs;
+    cudaGraphNode_t cn;
+    SPAI_CUDA(cudaGraphAddKernelNode(&cn, body, &kn, 1, &cpk));
+    SPAI_CUDA(cudaGraphInstantiate(&gr.e, gr.g, 0));
+    if (ev0) SPAI_CUDA(cudaEventRecord(ev0, s_));
+    SPAI_CUDA(cudaGraphLaunch(gr.e, s_));
+    if (ev1) SPAI_CUDA(cudaEventRecord(ev1, s_));
+    GridSync gh;
+    SPAI_CUDA(cudaMemcpyAsync(&gh, args_.gs, sizeof(gh), cudaMemcpyDeviceToHost, s_));
+    SPAI_CUDA(cudaStreamSynchronize(s_));
+    if (ev0 && ev1 && ms) {
+      float f = 0.f;
+      SPAI_CUDA(cudaEventElapsedTime(&f, ev0, ev1));
+      *ms += f;
+    }
+    *launches = gh.pad[0];
+    count_launch(2 * gh.pad[0]);
+    slots_ = gh.slot;
+    live_ = gh.live;
+    if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
     return SPAI_OK;
   }
 
@@ -1163,7 +1392,7 @@ void engine_fill_result(const EngState& f, double true_rel, double engine_ms, in
 
 // Runs PCG on nsys systems in one persistent launch sequence.
 int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const double* const* b, double* const* x,
-               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override) {
+               const spai_pcg_opts* o, spai_pcg_result* res, cudaStream_t s, int grid_override, int use_graph) {
   if (nsys <= 0) return set_error(SPAI_ERR_INVALID, "nsys must be positive");
   int rc;
   if ((rc = engine_check_opts(o))) return rc;
@@ -1202,11 +1431,15 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
     cudaEvent_t a, b;
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } evg{ev0, ev1};
-  while (B.live() > 0) {
-    const int64_t left = slot_cap - B.slots();
-    if (left <= 0) break;
-    if ((rc = B.launch((int)(left < chunk ? left : chunk), ev0, ev1, &engine_ms))) return rc;
-    ++launches;
+  if (use_graph) {
+    if ((rc = B.run_graph(chunk, slot_cap, ev0, ev1, &engine_ms, &launches))) return rc;
+  } else {
+    while (B.live() > 0) {
+      const int64_t left = slot_cap - B.slots();
+      if (left <= 0) break;
+      if ((rc = B.launch((int)(left < chunk ? left : chunk), ev0, ev1, &engine_ms))) return rc;
+      ++launches;
+    }
   }
   std::vector<EngState> fin;
   if ((rc = B.read_states(fin))) return rc;
@@ -1220,6 +1453,83 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   if (first_bad != SPAI_OK)
     set_error(first_bad, "pcg: %s", first_bad == SPAI_ERR_BREAKDOWN ? "breakdown" : "not converged");
   return first_bad;
+}
+
+namespace {
+__global__ void tune_rhs_kernel(double* b, double* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    b[i] = 1.0 + 0.25 * (double)(i % 5);
+    x[i] = 0.0;
+  }
+}
+}  // namespace
+
+// Schedule autotuner: times short solves (a fixed right-hand side, rtol 0,
+// kTuneIters iterations, best of two runs) of the system with the given
+// preconditioner and precision for every candidate schedule -- tile size
+// (entries per group) T0, T0/2, T0/4; groups per work item x1/2, x1, x2;
+// SELL-32 slices (when the matrices have the layout), TMA-staged CSR groups
+// or CSR with direct loads -- and keeps the fastest.  The heuristic
+// schedule is kept unless a candidate beats it by more than 3%.
+int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
+  constexpr int kTuneIters = 12;
+  const int32_t t0 = engine_tile_nnz(S->max_row);
+  struct Cand { int32_t tile, klog, staged, sell; };
+  std::vector<Cand> cands;
+  const bool has_sell = S->sell_a.nslices > 0 || M->P->sell.nslices > 0;
+  for (int div : {1, 2, 4}) {
+    const int32_t t = t0 / div;
+    if (div > 1 && t < 256) continue;
+    for (int kl : {0, -1, 1}) {
+      if (has_sell) cands.push_back(Cand{t, kl, 1, 1});
+      for (int st : {1, 0}) {
+        if (st == 0 && !engine_groups_fit(S->max_row)) continue;  // direct loads either way
+        cands.push_back(Cand{t, kl, st, 0});
+      }
+    }
+  }
+  DevMem buf;
+  int rc;
+  if ((rc = buf.alloc(2 * (size_t)S->n * sizeof(double), s))) return rc;
+  double* b = buf.as<double>();
+  double* x = b + S->n;
+  spai_pcg_opts o;
+  spai_pcg_opts_default(&o);
+  o.rtol = 0.0;
+  o.max_iter = kTuneIters;
+  o.precision = mixed ? SPAI_PREC_MIXED : SPAI_PREC_F64;
+  o.record_history = 0;
+  double best_t = 1e300, base_t = 1e300;
+  Cand best = cands[0];
+  for (const Cand& c : cands) {
+    S->tile_nnz = c.tile;
+    S->items_log2 = c.klog;
+    S->staged = c.staged;
+    S->sell = c.sell;
+    double t = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      tune_rhs_kernel<<<256, 256, 0, s>>>(b, x, S->n);
+      count_launch();
+      spai_pcg_result r;
+      const double* bc = b;
+      rc = engine_run(1, &S, &M, &bc, &x, &o, &r, s, 0, 0);
+      if (rc != SPAI_OK && rc != SPAI_ERR_NOT_CONVERGED) return rc;
+      if (r.engine_ms < t) t = r.engine_ms;
+    }
+    if (&c == &cands[0]) base_t = t;
+    if (t < best_t) {
+      best_t = t;
+      best = c;
+    }
+  }
+  if (best_t > 0.97 * base_t) best = cands[0];
+  S->tile_nnz = best.tile;
+  S->items_log2 = best.klog;
+  S->staged = best.staged;
+  S->sell = best.sell;
+  S->tuned = 1;
+  set_error(SPAI_OK, "no error");
+  return SPAI_OK;
 }
 
 }  // namespace spai
@@ -1428,6 +1738,7 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
     e.fits[k] = 0;  // caller arrays carry no alignment padding: direct loads
   }
   e.a_v64 = static_cast<const double*>(A->val);
+  e.a_ci64 = A->colidx;
   int ng = ntl[0] > ntl[1] ? ntl[0] : ntl[1];
   if (ntl[2] > ng) ng = ntl[2];
   const int kg = engine_items_k(ng, grid_max);

@@ -775,6 +775,7 @@ extern "C" int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const 
   std::shared_ptr<PrecondData> M;
   int rc = gnn_forward(A, P->d, node_feat, W, g_dtype, eps, M, (cudaStream_t)stream);
   if (rc) return rc;
+  if ((rc = precond_sell(*M, (cudaStream_t)stream))) return rc;
   *out = new spai_precond{M};
   return SPAI_OK;
 }

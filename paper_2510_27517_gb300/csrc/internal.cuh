@@ -52,6 +52,21 @@ size_t dtype_size(int dt);
 // ---------------------------------------------------------------------------
 // Handles
 // ---------------------------------------------------------------------------
+// SELL-32 layout of a CSR pattern: slices of 32 consecutive rows, each slice
+// stored column-major (entry k of the slice's 32 rows together) with the
+// width of its longest row.  Entry k of row i sits at
+// sptr[i / 32] + 32 k + i % 32; positions past a row's length are padding and
+// are never read.  Built only when every row has at most kSellMaxRow entries
+// and padding adds at most a quarter to the stored entries.
+constexpr int32_t kSellMaxRow = 64;
+struct SellData {
+  int32_t nslices = 0;         // 0: not available
+  int32_t max_width = 0;
+  int64_t total = 0;           // stored entries including padding
+  DevMem sptr;                 // nslices + 1 entry offsets (multiples of 32)
+  DevMem ci;                   // total column indices
+};
+
 struct PatternData {
   int64_t n = 0, nnz = 0;      // nnz of G
   int32_t kind = SPAI_PATTERN_FULL;
@@ -62,18 +77,22 @@ struct PatternData {
   DevMem perm;                 // val_T[perm[e]] = val[e]
   DevMem src;                  // index into A of each entry of G (LOWER/UPPER only)
   int64_t a_nnz = 0;           // nnz of the A it was built from
+  SellData sell;               // FULL patterns (shared by G and G^T)
   const int32_t* g_rp() const { return rowptr.as<int32_t>(); }
   const int32_t* g_ci() const { return colidx.as<int32_t>(); }
   const int32_t* gt_rp() const { return kind == SPAI_PATTERN_FULL ? rowptr.as<int32_t>() : t_rowptr.as<int32_t>(); }
   const int32_t* gt_ci() const { return kind == SPAI_PATTERN_FULL ? colidx.as<int32_t>() : t_colidx.as<int32_t>(); }
 };
 
-// Row-start table of one matrix for one tile size (built on demand, cached).
+// Row-start table of one matrix for one tile size (built on demand, cached
+// for the last (offset array, tile size) pair).
 struct TileSet {
   int32_t tile_nnz = 0;
   int32_t ntiles = 0;
-  DevMem starts;  // ntiles + 1 row indices
+  const void* src = nullptr;
+  DevMem starts;  // ntiles + 1 row (or slice) indices
 };
+
 
 struct PrecondData {
   std::shared_ptr<PatternData> P;
@@ -81,6 +100,7 @@ struct PrecondData {
   double eps = 0.0;
   double anorm = 0.0;        // ||A|| used by the GNN (0 when values were given)
   DevMem g_val, gt_val;
+  DevMem sell_g, sell_gt;    // values in the pattern's SELL-32 layout (when it has one)
   TileSet g_tiles, gt_tiles; // cached for the last tile size used
 };
 
@@ -88,10 +108,16 @@ struct SystemData {
   int64_t n = 0, nnz = 0;
   int32_t max_row = 0;
   DevMem rowptr, colidx, val64, val32;
-  int32_t tile_nnz = 2048;
-  int32_t block = 256;
-  int32_t grid_per_sm = 0;   // 0: as many co-resident blocks as fit
+  // SpMV schedule of the persistent solver (the same for A, G^T and G):
+  int32_t tile_nnz = 2048;   // entries per row group (one staging unit)
+  int32_t items_log2 = 0;    // groups per work item = heuristic count * 2^items_log2
+  int32_t staged = 1;        // 1: groups staged by TMA bulk copies (when rows fit), 0: direct loads
+  int32_t sell = 1;          // 1: SELL-32 layout for matrices that have one, 0: CSR row groups
+  int32_t autotune = 0;      // pick the schedule by timing candidates on the first solve
+  int32_t tuned = 0;
   TileSet tiles;
+  SellData sell_a;           // A in SELL-32 (pattern and float64 / float32 values)
+  DevMem sell_v64, sell_v32;
 };
 
 }  // namespace spai
@@ -107,6 +133,14 @@ int build_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz,
 int validate_csr_device(const spai_csr* A, bool need_symmetric, int32_t* max_row, cudaStream_t s);
 int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
 int system_from_csr(const spai_csr* A, SystemData& S, bool validate, cudaStream_t s);
+// SELL-32 pattern of a CSR (out.nslices stays 0 when the layout does not pay)
+int build_sell(const int32_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int32_t max_row, SellData& out,
+               cudaStream_t s);
+// values of a CSR (dtype dt_in) into the SELL-32 layout (dtype dt_out)
+int sell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val, int dt_in, void* out, int dt_out,
+                cudaStream_t s);
+// G and G^T values of a preconditioner in its pattern's SELL-32 layout
+int precond_sell(PrecondData& M, cudaStream_t s);
 int num_sms();
 
 // ---------------------------------------------------------------------------

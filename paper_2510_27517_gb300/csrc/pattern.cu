@@ -248,7 +248,7 @@ int validate_csr_device(const spai_csr* A, bool need_symmetric, int32_t* max_row
 
 int build_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz, TileSet& ts, cudaStream_t s) {
   if (tile_nnz <= 0) return set_error(SPAI_ERR_INVALID, "tile size must be positive");
-  if (ts.tile_nnz == tile_nnz && ts.starts.p) return SPAI_OK;
+  if (ts.tile_nnz == tile_nnz && ts.src == rowptr && ts.starts.p) return SPAI_OK;
   int64_t nt = (nnz + tile_nnz - 1) / tile_nnz;
   if (nt < 1) nt = 1;
   if (nt >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many tiles");
@@ -260,6 +260,7 @@ int build_tiles(const int32_t* rowptr, int64_t n, int64_t nnz, int32_t tile_nnz,
   ts.starts.keep();
   ts.ntiles = (int32_t)nt;
   ts.tile_nnz = tile_nnz;
+  ts.src = rowptr;
   return SPAI_OK;
 }
 
@@ -291,6 +292,126 @@ int system_from_csr(const spai_csr* A, SystemData& S, bool validate, cudaStream_
   S.tiles.starts.release();
   S.tiles.ntiles = 0;
   S.tiles.tile_nnz = 0;
+  return SPAI_OK;
+}
+
+namespace {
+// 32 x (longest row) of every 32-row slice; one warp per slice
+__global__ void sell_width_kernel(const int32_t* __restrict__ rp, int64_t n, int64_t nslices, int32_t* w32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nw) {
+    const int64_t row = sl * 32 + lane;
+    int len = row < n ? rp[row + 1] - rp[row] : 0;
+    for (int o = 16; o; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) w32[sl] = 32 * len;
+  }
+}
+
+__device__ __forceinline__ double ld_dt(const void* p, int dt, int64_t i) {
+  switch (dt) {
+    case SPAI_F64: return static_cast<const double*>(p)[i];
+    case SPAI_F32: return (double)static_cast<const float*>(p)[i];
+    case SPAI_BF16: return (double)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+    default: return (double)__half2float(static_cast<const __half*>(p)[i]);
+  }
+}
+
+// Stores v (exactly representable in dt whenever it came from dt or from a
+// float64 value rounded once to dt) at index i of an array of type dt.
+__device__ __forceinline__ void st_dt(void* p, int dt, int64_t i, double v) {
+  switch (dt) {
+    case SPAI_F64: static_cast<double*>(p)[i] = v; break;
+    case SPAI_F32: static_cast<float*>(p)[i] = (float)v; break;
+    case SPAI_BF16: static_cast<__nv_bfloat16*>(p)[i] = __double2bfloat16(v); break;
+    default: static_cast<__half*>(p)[i] = __double2half(v); break;
+  }
+}
+
+// One thread per row (rows up to 32 * nslices): the row's column indices
+// (and values, when val is given) at their SELL positions, zeros in padding.
+__global__ void sell_fill_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
+                                 int64_t nslices, const int32_t* __restrict__ sptr, int32_t* ci_out,
+                                 const void* val, int dt_in, void* val_out, int dt_out) {
+  const int64_t rows = nslices * 32;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = row >> 5;
+    const int lane = (int)(row & 31);
+    const int64_t off = sptr[sl];
+    const int w = (sptr[sl + 1] - sptr[sl]) >> 5;
+    const int64_t e0 = row < n ? rp[row] : 0;
+    const int len = row < n ? (int)(rp[row + 1] - e0) : 0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t pos = off + 32 * (int64_t)k + lane;
+      if (ci_out) ci_out[pos] = k < len ? ci[e0 + k] : 0;
+      if (val_out) st_dt(val_out, dt_out, pos, k < len ? ld_dt(val, dt_in, e0 + k) : 0.0);
+    }
+  }
+}
+}  // namespace
+
+int build_sell(const int32_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int32_t max_row, SellData& out,
+               cudaStream_t s) {
+  out.nslices = 0;
+  out.total = 0;
+  if (n <= 0 || max_row < 1 || max_row > kSellMaxRow) return SPAI_OK;
+  const int64_t ns = (n + 31) / 32;
+  if ((int64_t)32 * max_row * ns >= (int64_t)INT32_MAX - 1024) return SPAI_OK;
+  int rc;
+  DevMem w;
+  if ((rc = w.alloc((ns + 1) * sizeof(int32_t), s))) return rc;
+  SPAI_CUDA(cudaMemsetAsync(w.as<int32_t>() + ns, 0, sizeof(int32_t), s));
+  sell_width_kernel<<<grid_for(ns * 32, 256), 256, 0, s>>>(rp, n, ns, w.as<int32_t>()); count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  DevMem& sptr = out.sptr;
+  if ((rc = sptr.alloc((ns + 1 + 16) * sizeof(int32_t), s))) return rc;
+  SPAI_CUDA(cudaMemsetAsync(sptr.p, 0, (ns + 1 + 16) * sizeof(int32_t), s));
+  if ((rc = exclusive_scan_i32(w.as<int32_t>(), sptr.as<int32_t>(), ns + 1, s))) return rc;
+  int32_t total = 0;
+  SPAI_CUDA(cudaMemcpyAsync(&total, sptr.as<int32_t>() + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SPAI_CUDA(cudaStreamSynchronize(s));
+  if ((int64_t)total * 4 > nnz * 5) {  // padding would add more than a quarter
+    sptr.release();
+    return SPAI_OK;
+  }
+  const int64_t pad = 64;
+  if ((rc = out.ci.alloc((total + pad) * sizeof(int32_t), s))) return rc;
+  SPAI_CUDA(cudaMemsetAsync(out.ci.p, 0, (total + pad) * sizeof(int32_t), s));
+  sell_fill_kernel<<<grid_for(ns * 32, 256), 256, 0, s>>>(rp, ci, n, ns, sptr.as<int32_t>(), out.ci.as<int32_t>(),
+                                                          nullptr, 0, nullptr, 0); count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  out.sptr.keep();
+  out.ci.keep();
+  out.nslices = (int32_t)ns;
+  out.total = total;
+  out.max_width = max_row;
+  return SPAI_OK;
+}
+
+int sell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val, int dt_in, void* out, int dt_out,
+                cudaStream_t s) {
+  if (L.nslices <= 0) return set_error(SPAI_ERR_INVALID, "no SELL layout");
+  sell_fill_kernel<<<grid_for((int64_t)L.nslices * 32, 256), 256, 0, s>>>(
+      rp, nullptr, n, L.nslices, L.sptr.as<int32_t>(), nullptr, val, dt_in, out, dt_out); count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  return SPAI_OK;
+}
+
+int precond_sell(PrecondData& M, cudaStream_t s) {
+  const PatternData& P = *M.P;
+  if (P.kind != SPAI_PATTERN_FULL || P.sell.nslices <= 0) return SPAI_OK;
+  const size_t gs = dtype_size(M.gtype);
+  const size_t bytes = (size_t)(P.sell.total + 64) * gs;
+  int rc;
+  if ((rc = M.sell_g.alloc(bytes, s))) return rc;
+  if ((rc = M.sell_gt.alloc(bytes, s))) return rc;
+  SPAI_CUDA(cudaMemsetAsync(M.sell_g.p, 0, bytes, s));
+  SPAI_CUDA(cudaMemsetAsync(M.sell_gt.p, 0, bytes, s));
+  if ((rc = sell_values(P.sell, P.g_rp(), P.n, M.g_val.p, M.gtype, M.sell_g.p, M.gtype, s))) return rc;
+  if ((rc = sell_values(P.sell, P.gt_rp(), P.n, M.gt_val.p, M.gtype, M.sell_gt.p, M.gtype, s))) return rc;
+  M.sell_g.keep();
+  M.sell_gt.keep();
   return SPAI_OK;
 }
 
@@ -330,6 +451,7 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
     perm_kernel<<<grid_for(n, block), block, 0, s>>>(P->g_rp(), P->g_ci(), P->g_rp(), P->g_ci(), n,
                                                      P->perm.as<int32_t>(), flags.as<int>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
+    if ((rc = build_sell(P->g_rp(), P->g_ci(), n, A->nnz, max_row, P->sell, s))) return rc;
   } else {
     const int lower_g = (kind == SPAI_PATTERN_LOWER) ? 1 : 0;
     DevMem cnt;

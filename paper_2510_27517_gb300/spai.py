@@ -56,6 +56,11 @@ class _Res(C.Structure):
                 ("engine_ms", C.c_double), ("slots", C.c_int64), ("launches", C.c_int32), ("pad", C.c_int32)]
 
 
+class _Sched(C.Structure):
+    _fields_ = [("tile_nnz", C.c_int32), ("items_log2", C.c_int32), ("staged", C.c_int32), ("sell", C.c_int32),
+                ("tuned", C.c_int32)]
+
+
 class _ServeCfg(C.Structure):
     _fields_ = [("hbm_cap_bytes", C.c_int64), ("max_slots", C.c_int32), ("chunk_iters", C.c_int32),
                 ("opts", _Opts)]
@@ -87,7 +92,8 @@ _SIGS = {
     "spai_precond_matrix_norm": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "spai_precond_destroy": (None, [C.c_void_p]),
     "spai_system_create": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
-    "spai_system_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "spai_system_schedule": (C.c_int, [C.c_void_p, C.POINTER(_Sched)]),
+    "spai_system_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(_Sched)]),
     "spai_system_destroy": (None, [C.c_void_p]),
     "spai_pcg_solve": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts),
                                  C.POINTER(_Res), C.c_void_p]),
@@ -235,9 +241,13 @@ class System(_Handle):
         self.A = A
 
     def schedule(self):
-        t, b = C.c_int32(), C.c_int32()
-        _check(lib().spai_system_schedule(self.h, C.byref(t), C.byref(b)))
-        return t.value, b.value
+        sc = _Sched()
+        _check(lib().spai_system_schedule(self.h, C.byref(sc)))
+        return {k: getattr(sc, k) for k, _ in _Sched._fields_}
+
+    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1):
+        sc = _Sched(tile_nnz, items_log2, staged, sell, 0)
+        _check(lib().spai_system_set_schedule(self.h, C.byref(sc)))
 
 
 def build_pattern(A: CSRMatrix, kind=PATTERN_FULL, stream=None) -> Pattern:

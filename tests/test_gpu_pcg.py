@@ -198,3 +198,74 @@ def test_mixed_reliable_updates_track_f64_iteration_count(spai_lib):
     assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x32, b) <= 1e-8
     assert r32["iters"] <= 1.3 * r64["iters"] + 10, (r32["iters"], r64["iters"])
     assert r32["outer_iters"] >= 1
+
+
+def test_autotuned_schedule_fixed_and_batch_consistent(spai_lib):
+    # the first solve of an autotuned system picks its schedule by timing;
+    # afterwards the schedule is fixed: the same result alone and in a batch
+    spai = spai_lib
+    A = W.aniso2d(150, 50.0, 0.9)
+    dA = upload(spai, A)
+    S = spai.system_create(dA, autotune=True)
+    assert S.schedule()["tuned"] == 0
+    M, _ = fsai_precond(spai, A, dA)
+    b = torch.tensor(W.rhs_uniform(A.n, 21), device="cuda")
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r1 = spai.system_solve(S, M, b, x)
+    sch = S.schedule()
+    assert sch["tuned"] == 1 and sch["tile_nnz"] >= 256 and sch["items_log2"] in (-1, 0, 1)
+    assert r1["status"] == 0
+    assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x.cpu().numpy(), b.cpu().numpy()) <= 1e-8
+    x2 = torch.zeros_like(x)
+    r2 = spai.system_solve(S, M, b, x2)
+    assert S.schedule() == sch and r2["iters"] == r1["iters"] and torch.equal(x, x2)
+    B = W.poisson2d(40)
+    dB = upload(spai, B)
+    SB = spai.system_create(dB)
+    MB, _ = fsai_precond(spai, B, dB)
+    bB = torch.tensor(W.rhs_uniform(B.n, 22), device="cuda")
+    xs = [torch.zeros_like(x), torch.zeros(B.n, dtype=torch.float64, device="cuda")]
+    res = spai.pcg_solve_batched([S, SB], [M, MB], [b, bB], xs)
+    assert res[0]["iters"] == r1["iters"] and torch.equal(xs[0], x)
+    assert res[1]["status"] == 0
+
+
+@pytest.mark.parametrize("sched", [dict(sell=1), dict(sell=0, staged=1), dict(sell=0, staged=0),
+                                   dict(sell=1, tile_nnz=300, items_log2=2), dict(sell=0, tile_nnz=257, items_log2=-2)])
+def test_every_schedule_matches_oracle(spai_lib, sched):
+    # SELL-32 slices and CSR row groups (staged or direct), any group size:
+    # the same float64 iteration as the oracle's Algorithm 1
+    spai = spai_lib
+    A, k = W.diffusion3d(12)
+    v = W.diffusion3d_node_features(k)
+    dA = upload(spai, A)
+    S = spai.system_create(dA)
+    S.set_schedule(**sched)
+    assert S.schedule()["tuned"] == 1
+    P = spai.build_pattern(dA, spai.PATTERN_FULL)
+    M = spai.gnn_precond(dA, P, torch.tensor(v, device="cuda"),
+                         torch.tensor(W.gnn_random_weights(4, 4), device="cuda"), d_node=4, g_dtype=spai.F64, eps=0.3)
+    g, _ = M.export(spai.F64)
+    b = W.rhs_uniform(A.n, 31)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, A.rowptr, A.colidx, g.cpu().numpy(), 0.3),
+                  rtol=1e-8)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    h = torch.zeros(20000, dtype=torch.float64, device="cuda")
+    r = spai.system_solve(S, M, torch.tensor(b, device="cuda"), x, history=h)
+    assert r["status"] == 0 and abs(r["iters"] - ref.iters) <= 0.01 * ref.iters + 1
+    # long runs: the first 200 iterations to the per-iteration bar, then the
+    # iteration count and the final accuracy
+    k0 = min(200, len(ref.history), r["history_written"])
+    assert_history_parity(h[:k0].cpu().numpy(), ref.history[:k0], np.linalg.norm(b))
+    xh = x.cpu().numpy()
+    assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, xh, b) <= 1e-8
+    assert np.linalg.norm(xh - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+
+
+def test_set_schedule_rejects_out_of_range(spai_lib):
+    spai = spai_lib
+    A = W.poisson2d(16)
+    S = spai.system_create(upload(spai, A))
+    for bad in (dict(tile_nnz=5000), dict(items_log2=5), dict(staged=2), dict(sell=-1)):
+        with pytest.raises(spai.SpaiError):
+            S.set_schedule(**bad)
