@@ -108,7 +108,8 @@ def gaussian_random_field(shape, corr_len: float, seed: int) -> np.ndarray:
 
     White N(0,1) noise convolved (via FFT, separably) with a Gaussian kernel of
     standard deviation corr_len / sqrt(2) cells, then renormalised to zero mean
-    and unit sample standard deviation.
+    and unit sample standard deviation (a constant zero field when the grid is
+    so much smaller than the correlation length that no variation survives).
     """
     g = rng(seed)
     w = g.standard_normal(shape)
@@ -122,7 +123,10 @@ def gaussian_random_field(shape, corr_len: float, seed: int) -> np.ndarray:
         f = f * kern.reshape(sh)
     field = np.real(np.fft.ifftn(f))
     field -= field.mean()
-    field /= field.std()
+    sd_f = field.std()
+    if not sd_f > 1e-12:   # grid much smaller than the correlation length: a constant field
+        return np.zeros(shape)
+    field /= sd_f
     return field
 
 
