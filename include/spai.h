@@ -119,6 +119,11 @@ typedef struct {
   int32_t record_history;  /* nonzero: write ||r|| after every iteration into `history` */
   double* history;         /* device, history_len doubles (history[0] = ||r_0||), may be NULL */
   int64_t history_len;
+  double* lanczos;         /* device, 2 lanczos_len doubles or NULL: the step length alpha_k of
+                              iteration k at [2k] and the ratio beta_k = delta_{k+1} / delta_k that
+                              follows it at [2k+1] (the CG / Lanczos coefficients, for
+                              spai_ritz_extremes); single-system solves only */
+  int64_t lanczos_len;
 } spai_pcg_opts;
 
 typedef struct {
@@ -132,7 +137,31 @@ typedef struct {
   int64_t slots;         /* grid-wide phases the persistent kernel executed */
   int32_t launches;      /* persistent kernel launches of this solve */
   int32_t pad;
+  int64_t lanczos_written; /* alpha values written to opts->lanczos (betas: one fewer, or as many) */
 } spai_pcg_result;
+
+/* ------------------------------------------------------------------------ *
+ * Condition-number estimates from a solve's own coefficients (Sec. 4.5
+ * measures preconditioners by kappa and Kaporin's condition number of
+ * A M^-1).  PCG's step lengths alpha_j and ratios beta_j define the
+ * tridiagonal Lanczos matrix T_k of M^-1 A:
+ *   T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},  T[j][j+1] = sqrt(beta_j)/alpha_j.
+ * Host functions (no device work); alpha has k entries, beta k - 1 (host
+ * arrays, e.g. copied from opts->lanczos).  SPAI_ERR_INVALID for k < 1 or a
+ * non-positive or non-finite coefficient.
+ * ------------------------------------------------------------------------ */
+/* Smallest and largest eigenvalue of T_k (Ritz values: inside the spectrum
+ * of M^-1 A, the extremes converge first), by Sturm-sequence bisection;
+ * kappa is estimated by *lam_max / *lam_min. */
+int spai_ritz_extremes(const double* alpha, const double* beta, int64_t k, double* lam_min, double* lam_max);
+
+/* Kaporin's condition number estimated by Gauss quadrature with T_m,
+ * m = min(k, 400): (sum_i w_i theta_i) / exp(sum_i w_i log theta_i) with
+ * Ritz values theta_i and weights w_i the squared first components of T_m's
+ * eigenvectors -- the arithmetic over the geometric mean of the spectrum
+ * weighted by the solve's normalised starting residual (an unbiased-in-
+ * expectation stand-in for the plain means when that residual is random). */
+int spai_ritz_kaporin(const double* alpha, const double* beta, int64_t k, double* kaporin);
 
 /* Fills `o` with the defaults (rtol 1e-8, replace_period 50, RESIDUAL, F64). */
 void spai_pcg_opts_default(spai_pcg_opts* o);

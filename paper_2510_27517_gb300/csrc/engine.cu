@@ -80,6 +80,8 @@ struct EngSys {
   void* rin;
   double* history;
   int64_t history_len;
+  double* lanczos;
+  int64_t lanczos_len;
 };
 
 struct EngOpts {
@@ -727,6 +729,7 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
         st.delta0 = dn;
       } else {
         st.beta = dn / st.delta;
+        if (S.lanczos && st.iter >= 1 && st.iter <= S.lanczos_len) S.lanczos[2 * (st.iter - 1) + 1] = st.beta;
       }
       st.delta = dn;
       if (o.criterion == SPAI_CRIT_PRECOND && !(dn > o.tol2 * st.delta0)) {
@@ -743,6 +746,7 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
       st.dc ^= 1;
       if (!(dq > 0.0) || !isfinite(dq)) { finish(SPAI_ERR_BREAKDOWN); return; }
       st.alpha = st.delta / dq;
+      if (S.lanczos && st.iter < S.lanczos_len) S.lanczos[2 * st.iter] = st.alpha;
       st.phase = (o.period > 0 && (st.iter % o.period) == 0) ? PH_P2X : PH_P2;
       return;
     }
@@ -1023,6 +1027,8 @@ class EngineBatch {
     void* work;              // engine_work_bytes(n, mixed) bytes of device memory
     double* history;
     int64_t history_len;
+    double* lanczos;
+    int64_t lanczos_len;
     EngState st;             // state to start from (fresh or carried over)
   };
 
@@ -1150,6 +1156,8 @@ class EngineBatch {
       if (mixed_) { e.e = base + 7 * stride; e.rin = base + 8 * stride; }
       e.history = mb.history;
       e.history_len = mb.history_len;
+      e.lanczos = mb.lanczos;
+      e.lanczos_len = mb.lanczos_len;
       if (A.n > nmax) nmax = A.n;
       if (mb.st.phase != PH_DONE) ++live;
     }
@@ -1417,6 +1425,8 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
     m.work = ws[i].p;
     m.history = (nsys == 1 && o->record_history) ? o->history : nullptr;
     m.history_len = (nsys == 1 && o->record_history) ? o->history_len : 0;
+    m.lanczos = (nsys == 1 && o->lanczos && o->lanczos_len > 0) ? o->lanczos : nullptr;
+    m.lanczos_len = m.lanczos ? o->lanczos_len : 0;
     m.st = EngineBatch::fresh_state(mixed);
   }
   if ((rc = B.set_members(mem, grid_override))) return rc;
@@ -1448,6 +1458,7 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   int first_bad = SPAI_OK;
   for (int i = 0; i < nsys; ++i) {
     engine_fill_result(fin[i], tr[i], engine_ms, B.slots(), launches, res[i]);
+    if (mem[i].lanczos) res[i].lanczos_written = fin[i].iter < mem[i].lanczos_len ? fin[i].iter : mem[i].lanczos_len;
     if (res[i].status != SPAI_OK && first_bad == SPAI_OK) first_bad = res[i].status;
   }
   if (first_bad != SPAI_OK)
@@ -1586,6 +1597,8 @@ int session_set(EngineSession* es, std::vector<SessionMember>& members) {
     m.work = sm.work;
     m.history = nullptr;
     m.history_len = 0;
+    m.lanczos = nullptr;
+    m.lanczos_len = 0;
     if (sm.state.size() == sizeof(EngState)) memcpy(&m.st, sm.state.data(), sizeof(EngState));
     else m.st = EngineBatch::fresh_state(es->mixed);
   }
@@ -1754,6 +1767,10 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
     e.history = o->history;
     e.history_len = o->history_len;
   }
+  if (o->lanczos && o->lanczos_len > 0) {
+    e.lanczos = o->lanczos;
+    e.lanczos_len = o->lanczos_len;
+  }
   const int items = e.nitems, chunks = (e.nitems + kChunk - 1) / kChunk;
   const size_t off_sys = off; off += al(sizeof(EngSys));
   const size_t off_st0 = off; off += al(sizeof(EngState));
@@ -1863,6 +1880,7 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
   res->true_rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
   res->rec_rel_res = fin.bb > 0 ? sqrt(fin.rr / fin.bb) : 0.0;
   res->history_written = fin.hist_n;
+  if (e.lanczos) res->lanczos_written = fin.iter < e.lanczos_len ? fin.iter : e.lanczos_len;
   res->engine_ms = 0.0;
   res->slots = done_slots;
   res->launches = launches;

@@ -47,13 +47,14 @@ class _Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int64), ("replace_period", C.c_int32),
                 ("criterion", C.c_int32), ("precision", C.c_int32), ("inner_rtol", C.c_double),
                 ("max_outer", C.c_int32), ("record_history", C.c_int32), ("history", C.c_void_p),
-                ("history_len", C.c_int64)]
+                ("history_len", C.c_int64), ("lanczos", C.c_void_p), ("lanczos_len", C.c_int64)]
 
 
 class _Res(C.Structure):
     _fields_ = [("iters", C.c_int64), ("outer_iters", C.c_int32), ("status", C.c_int32),
                 ("true_rel_res", C.c_double), ("rec_rel_res", C.c_double), ("history_written", C.c_int64),
-                ("engine_ms", C.c_double), ("slots", C.c_int64), ("launches", C.c_int32), ("pad", C.c_int32)]
+                ("engine_ms", C.c_double), ("slots", C.c_int64), ("launches", C.c_int32), ("pad", C.c_int32),
+                ("lanczos_written", C.c_int64)]
 
 
 class _Sched(C.Structure):
@@ -80,6 +81,9 @@ _SIGS = {
     "spai_version": (C.c_char_p, []),
     "spai_kernel_launches": (C.c_uint64, []),
     "spai_pcg_opts_default": (None, [C.POINTER(_Opts)]),
+    "spai_ritz_extremes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
+    "spai_ritz_kaporin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "spai_build_pattern": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_pattern_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spai_pattern_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
@@ -282,7 +286,8 @@ def system_create(A: CSRMatrix, autotune=False, stream=None) -> System:
 
 
 def make_opts(rtol=1e-8, max_iter=0, replace_period=50, criterion=CRIT_RESIDUAL, precision=PREC_F64,
-              inner_rtol=0.1, max_outer=0, history: torch.Tensor | None = None) -> _Opts:
+              inner_rtol=0.1, max_outer=0, history: torch.Tensor | None = None,
+              lanczos: torch.Tensor | None = None) -> _Opts:
     o = _Opts()
     lib().spai_pcg_opts_default(C.byref(o))
     o.rtol, o.max_iter, o.replace_period, o.criterion = rtol, max_iter, replace_period, criterion
@@ -290,13 +295,39 @@ def make_opts(rtol=1e-8, max_iter=0, replace_period=50, criterion=CRIT_RESIDUAL,
     if history is not None:
         assert history.dtype == torch.float64 and history.is_cuda
         o.record_history, o.history, o.history_len = 1, history.data_ptr(), history.numel()
+    if lanczos is not None:
+        assert lanczos.dtype == torch.float64 and lanczos.is_cuda and lanczos.numel() % 2 == 0
+        o.lanczos, o.lanczos_len = lanczos.data_ptr(), lanczos.numel() // 2
     return o
+
+
+def _host_f64(a):
+    t = torch.as_tensor(a, dtype=torch.float64).cpu().contiguous()
+    return t, C.c_void_p(t.data_ptr())
+
+
+def ritz_extremes(alpha, beta):
+    """(lam_min, lam_max) of the Lanczos matrix of k PCG steps (spai_ritz_extremes)."""
+    ta, pa = _host_f64(alpha)
+    tb, pb = _host_f64(beta)
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().spai_ritz_extremes(pa, pb, ta.numel(), C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def ritz_kaporin(alpha, beta):
+    """Kaporin's condition number by Gauss quadrature on the Lanczos matrix."""
+    ta, pa = _host_f64(alpha)
+    tb, pb = _host_f64(beta)
+    v = C.c_double()
+    _check(lib().spai_ritz_kaporin(pa, pb, ta.numel(), C.byref(v)))
+    return v.value
 
 
 def _res_dict(r: _Res):
     return {"iters": r.iters, "outer_iters": r.outer_iters, "status": r.status, "true_rel_res": r.true_rel_res,
             "rec_rel_res": r.rec_rel_res, "history_written": r.history_written, "engine_ms": r.engine_ms,
-            "slots": r.slots, "launches": r.launches}
+            "slots": r.slots, "launches": r.launches, "lanczos_written": r.lanczos_written}
 
 
 def kernel_launches() -> int:

@@ -284,3 +284,33 @@ def test_set_schedule_rejects_out_of_range(spai_lib):
     for bad in (dict(tile_nnz=5000), dict(items_log2=5), dict(staged=2), dict(sell=-1)):
         with pytest.raises(spai.SpaiError):
             S.set_schedule(**bad)
+
+
+def test_lanczos_coefficients_and_condition_estimates(spai_lib):
+    # the solve's alpha / beta against the oracle's, and the Ritz estimates of
+    # kappa and Kaporin's number (Sec. 4.5) against the dense spectrum
+    from oracle import spectrum
+    spai = spai_lib
+    A = W.poisson2d(32)
+    b = W.rhs_uniform(A.n, 41)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, urp, uci, gv, 0.0), rtol=1e-10)
+    lz = torch.zeros(2 * 4096, dtype=torch.float64, device="cuda")
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = spai.pcg_solve(dA, M, torch.tensor(b, device="cuda"), x, rtol=1e-10, lanczos=lz)
+    k = r["lanczos_written"]
+    assert r["status"] == 0 and k == r["iters"] == ref.iters == len(ref.alphas)
+    al = lz[0::2][:k].cpu().numpy()
+    be = lz[1::2][:k - 1].cpu().numpy()
+    assert np.allclose(al, ref.alphas, rtol=1e-9)
+    assert np.allclose(be, ref.betas[:k - 1], rtol=1e-9)
+    lam = spectrum.preconditioned_eigenvalues(A.n, A.rowptr, A.colidx, A.val, urp, uci, gv, 0.0)
+    lo, hi = spai.ritz_extremes(al, be)
+    assert lo >= lam[0] * (1 - 1e-9) and hi <= lam[-1] * (1 + 1e-9)
+    assert hi / lo == pytest.approx(spectrum.kappa(lam), rel=1e-2)
+    ritz_o = spectrum.ritz_values(ref.alphas, ref.betas[:k - 1])
+    assert hi / lo == pytest.approx(ritz_o.max() / ritz_o.min(), rel=1e-8)
+    kap = spai.ritz_kaporin(al, be)
+    assert 1.0 < kap < hi / lo
+    assert kap == pytest.approx(spectrum.kappa_kaporin(lam), rel=0.25)
