@@ -15,9 +15,11 @@
 //           confirm convergence), r.r
 //   APPLY1  t = G^T r after a RESID
 //
-// so a regular iteration costs three passes and three grid barriers.  The
-// vector updates round exactly like "a + b*c" evaluated as two operations and
-// values that are both stored and recomputed on the fly (r', p) use the same
+// so a regular iteration costs three passes and three grid barriers.  Row
+// sums accumulate entry by entry in stored order with fused multiply-adds, and
+// the vector updates a + b*c are single fused multiply-adds (one rounding each:
+// on this GPU float64 instructions are scarce, and fusing halves them); values
+// that are both stored and recomputed on the fly (r', p) use the same
 // expression, so every block sees bit-identical values.
 //
 // Mixed precision (SPAI_PREC_MIXED): the same iteration runs on float32 A, G
@@ -167,7 +169,7 @@ __device__ __forceinline__ void spmv_group(const int32_t* __restrict__ rp, const
 #pragma unroll
     for (int u = 0; u < kNE; ++u) {
       const int k = threadIdx.x + u * kBlock;
-      if (k < m) sbuf[k] = rmul(v[u], g[u]);
+      if (k < m) sbuf[k] = g[u];
     }
   }
   __syncthreads();
@@ -182,7 +184,7 @@ __device__ __forceinline__ void spmv_group(const int32_t* __restrict__ rp, const
       const int a0 = __ldg(rp + row) - base, a1 = __ldg(rp + row + 1) - base;
       const typename Op::Pre q = op.pre(row);
       AT sum = AT(0);
-      for (int e = a0; e < a1; ++e) sum = radd(sum, sbuf[e]);
+      for (int e = a0; e < a1; ++e) sum = rfma(Conv<AT>::f(ldro(val + base + e)), sbuf[e], sum);
       op.fin(row, sum, q, p0, p1);
     }
   }
@@ -218,7 +220,7 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
       const int e1 = __ldg(rp + r + 1);
       double acc = 0.0;
       for (int e = base + threadIdx.x; e < e1; e += blockDim.x)
-        acc += (double)rmul(Conv<AT>::f(ldro(val + e)), op.gather(__ldg(ci + e)));
+        acc = rfma((double)Conv<AT>::f(ldro(val + e)), (double)op.gather(__ldg(ci + e)), acc);
       acc = block_sum(acc, red);
       if (threadIdx.x == 0) {
         const typename Op::Pre pr = op.pre(r);
@@ -239,11 +241,11 @@ template <class VT> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
   struct Pre { VT sv, dv; };
   __device__ VT gather(int c) const {
     const VT sv = ldv(s + c);
-    return first ? sv : radd(sv, rmul(beta, ldv(dcur + c)));
+    return first ? sv : rfma(beta, ldv(dcur + c), sv);
   }
   __device__ Pre pre(int row) const { return Pre{ldv(s + row), first ? VT(0) : ldv(dcur + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
-    const VT pv = first ? p.sv : radd(p.sv, rmul(beta, p.dv));
+    const VT pv = first ? p.sv : rfma(beta, p.dv, p.sv);
     dnxt[row] = pv;
     q[row] = sum;
     p0 += (double)pv * (double)sum;
@@ -252,11 +254,11 @@ template <class VT> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
 template <class VT> struct OpP2 {   // x += alpha d;  r' = r - alpha q;  t = G^T r';  r'.r'
   const VT* rcur; VT* rnxt; const VT* q; const VT* dcur; VT* x; VT* t; VT alpha;
   struct Pre { VT xv, dv, rv, qv; };
-  __device__ VT gather(int c) const { return rsub(ldv(rcur + c), rmul(alpha, ldv(q + c))); }
+  __device__ VT gather(int c) const { return rfma(-alpha, ldv(q + c), ldv(rcur + c)); }
   __device__ Pre pre(int row) const { return Pre{ldv(x + row), ldv(dcur + row), ldv(rcur + row), ldv(q + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
-    x[row] = radd(p.xv, rmul(alpha, p.dv));
-    const VT rn = rsub(p.rv, rmul(alpha, p.qv));
+    x[row] = rfma(alpha, p.dv, p.xv);
+    const VT rn = rfma(-alpha, p.qv, p.rv);
     rnxt[row] = rn;
     t[row] = sum;
     p0 += (double)rn * (double)rn;
@@ -275,7 +277,7 @@ template <class VT> struct OpApply2 {   // s = G t + eps r;  r.s
   __device__ VT gather(int c) const { return ldv(t + c); }
   __device__ Pre pre(int row) const { return Pre{ldv(r + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
-    const VT sv = radd(sum, rmul(eps, p.rv));
+    const VT sv = rfma(eps, p.rv, sum);
     s[row] = sv;
     p0 += (double)p.rv * (double)sv;
   }
@@ -441,12 +443,12 @@ __device__ __forceinline__ void piped_groups(Pipe& P, const int32_t* __restrict_
 #pragma unroll
         for (int u = 0; u < kWarpE / 32; ++u) {
           const int kk = lane + 32 * u;
-          if (kk < m) wb[kk] = rmul(Conv<AT>::f(vs[cb + kk]), g[u]);
+          if (kk < m) wb[kk] = g[u];
         }
         __syncwarp();
         if (valid) {
           const int lo = max(ea, cb), hi = min(eb, cb + m);
-          for (int e = lo; e < hi; ++e) acc = radd(acc, wb[e - cb]);
+          for (int e = lo; e < hi; ++e) acc = rfma(Conv<AT>::f(vs[e]), wb[e - cb], acc);
         }
         __syncwarp();
       }
@@ -524,16 +526,12 @@ __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict_
       const MV* vl = vs + off + lane;
       AT acc = AT(0);
       for (int k0 = 0; k0 < w; k0 += kB) {
-        AT prod[kB];
+        AT gv[kB];  // all gathers of the batch in flight before the sums
 #pragma unroll
-        for (int u = 0; u < kB; ++u) {
-          const int kk = k0 + u;
-          prod[u] = AT(0);
-          if (kk < len) prod[u] = rmul(Conv<AT>::f(vl[32 * kk]), op.gather(cl[32 * kk]));
-        }
+        for (int u = 0; u < kB; ++u) gv[u] = (k0 + u < len) ? op.gather(cl[32 * (k0 + u)]) : AT(0);
 #pragma unroll
         for (int u = 0; u < kB; ++u)
-          if (k0 + u < len) acc = radd(acc, prod[u]);
+          if (k0 + u < len) acc = rfma(Conv<AT>::f(vl[32 * (k0 + u)]), gv[u], acc);
       }
       if (valid) op.fin(row, acc, pr, p0, p1);
     }
@@ -561,6 +559,16 @@ __device__ __noinline__ void direct_groups(const int32_t* __restrict__ tiles, co
   uint32_t blocks = 0;
   for (int g = g0; g < g1; ++g)
     spmv_rows<AT>(rp, ci, val, __ldg(tiles + g), __ldg(tiles + g + 1), sbuf, red, op, p0, p1, blocks);
+}
+
+// Rows [r0, r1) without the stage ring (float64 residual of mixed precision
+// over SELL-32 slices): direct loads.
+template <class AT, class MV, class Op>
+__device__ __noinline__ void direct_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const MV* __restrict__ val, int r0, int r1, AT* sbuf, double* red,
+                                         const Op& op, double& p0, double& p1) {
+  uint32_t blocks = 0;
+  spmv_rows<AT>(rp, ci, val, r0, r1, sbuf, red, op, p0, p1, blocks);
 }
 
 template <class AT, class MV, class Op>
@@ -631,16 +639,17 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
       break;
     }
     case PH_RESID64: {
-      OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
-      if (sp) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
-        uint32_t blocks = 0;
-        const int r0 = __ldg(tl + g0) * 32, r1 = (int)min((int64_t)__ldg(tl + g1) * 32, n);
-        if (r0 < r1)
-          spmv_rows<double>(S.rp[MAT_A], S.a_ci64, S.a_v64, r0, r1, reinterpret_cast<double*>(sbuf), red, op, p0,
-                            p1, blocks);
-      } else {
-        direct_groups<double>(tl, S.rp[MAT_A], S.a_ci64, S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red,
-                              op, p0, p1);
+      if constexpr (MIXED) {
+        OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
+        if (sp) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
+          const int r0 = __ldg(tl + g0) * 32, r1 = (int)min((int64_t)__ldg(tl + g1) * 32, n);
+          if (r0 < r1)
+            direct_rows<double>(S.rp[MAT_A], S.a_ci64, S.a_v64, r0, r1, reinterpret_cast<double*>(sbuf), red, op,
+                                p0, p1);
+        } else {
+          direct_groups<double>(tl, S.rp[MAT_A], S.a_ci64, S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red,
+                                op, p0, p1);
+        }
       }
       break;
     }
@@ -650,7 +659,7 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
       const int r0 = sp ? __ldg(tl + g0) * 32 : __ldg(tl + g0);
       const int r1 = sp ? (int)min((int64_t)__ldg(tl + g1) * 32, n) : __ldg(tl + g1);
       for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-        if (ph == PH_P2X) xv[row] = radd(ldv(xv + row), rmul(alpha, ldv(d_cur + row)));
+        if (ph == PH_P2X) xv[row] = rfma(alpha, ldv(d_cur + row), ldv(xv + row));
         else if (ph == PH_XUPD) {
           S.x[row] = __dadd_rn(ldv(S.x + row), (double)ldv(xv + row));
           xv[row] = VT(0);
@@ -916,7 +925,7 @@ __global__ void true_residual_kernel(const int32_t* __restrict__ rp, const int32
   double rr = 0.0, bb = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) s = __dadd_rn(s, __dmul_rn(v[e], x[ci[e]]));
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s = __fma_rn(v[e], x[ci[e]], s);
     const double r = b[i] - s;
     rr += r * r;
     bb += b[i] * b[i];

@@ -208,6 +208,9 @@ __device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+// a * b + c with one rounding
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -307,9 +310,12 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch
   __syncthreads();
 }
 
-// Grid-wide barrier for cooperative launches with a bounded wait.
+// Grid-wide barrier for cooperative launches with a bounded wait.  (A
+// two-level arrival count -- per-group counters, then a counter of groups --
+// measured slower on GB300 than one counter: the last arriver's chain of two
+// atomics outweighs the serialised arrivals.)
 struct GridSync {
-  unsigned count;
+  unsigned count;  // blocks arrived
   unsigned gen;
   int exit_flag;   // decided by the last arriver, read by everyone after the barrier
   int err;         // SPAI_ERR_TIMEOUT when a wait gave up
