@@ -163,6 +163,19 @@ int spai_ritz_extremes(const double* alpha, const double* beta, int64_t k, doubl
  * expectation stand-in for the plain means when that residual is random). */
 int spai_ritz_kaporin(const double* alpha, const double* beta, int64_t k, double* kaporin);
 
+/* ------------------------------------------------------------------------ *
+ * sai_loss - the scale-invariant aligned-identity loss of Sec. 3.3 (Eq. 8)
+ * with Hutchinson probes (Eq. 7), the quantity the paper trains G on:
+ *   loss[j] = || A (G G^T + eps I) w_j / ||A|| - w_j ||_2^2,  j < k,
+ * ||A|| = mean |A_ij| over stored entries.  A: device CSR (F64); M: any
+ * preconditioner (its G^T, G and eps); w: device float64, n x k with the
+ * probe index fastest (w[i * k + j] = entry i of probe j), 1 <= k <= 32;
+ * loss: device float64[k].  Forward value only, float64 arithmetic, fixed
+ * summation order.  Errors: SPAI_ERR_INVALID (k, null, dtype),
+ * SPAI_ERR_SHAPE (sizes differ).
+ * ------------------------------------------------------------------------ */
+int spai_sai_loss(const spai_csr* A, const spai_precond* M, const double* w, int32_t k, double* loss, void* stream);
+
 /* Fills `o` with the defaults (rtol 1e-8, replace_period 50, RESIDUAL, F64). */
 void spai_pcg_opts_default(spai_pcg_opts* o);
 

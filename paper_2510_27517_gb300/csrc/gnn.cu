@@ -528,6 +528,19 @@ struct MLPView {
 
 }  // namespace
 
+// ||A|| (Sec. 3.3) into out[0] on the device; the same deterministic sum
+// everywhere it is needed.
+int matrix_abs_mean(const double* val, int64_t nnz, double* out, cudaStream_t s) {
+  const int npart = 4 * num_sms();
+  DevMem part;
+  int rc;
+  if ((rc = part.alloc(sizeof(double) * npart, s))) return rc;
+  abs_partial_kernel<<<npart, 256, 0, s>>>(val, nnz, part.as<double>()); count_launch();
+  abs_final_kernel<<<1, 256, 0, s>>>(part.as<double>(), npart, nnz, out); count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  return SPAI_OK;
+}
+
 int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const float* node_feat,
                 const spai_gnn_weights* W, int g_dtype, double eps, std::shared_ptr<PrecondData>& out,
                 cudaStream_t s) {
@@ -598,19 +611,15 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
 
   // workspace
   const int64_t nnz32 = (nnz + 31) / 32 * 32;
-  DevMem hbuf, xbuf, pqe, pqm, sbuf, normb, part;
-  const int npart = 4 * num_sms();
+  DevMem hbuf, xbuf, pqe, pqm, sbuf, normb;
   if ((rc = normb.alloc(sizeof(double) * 2, s))) return rc;
-  if ((rc = part.alloc(sizeof(double) * npart, s))) return rc;
   if (L > 0 && (rc = hbuf.alloc((size_t)nnz32 * H * sizeof(float), s))) return rc;
   if ((rc = xbuf.alloc((size_t)n * H * sizeof(float), s))) return rc;
   if ((rc = pqe.alloc((size_t)n * 2 * H * sizeof(float), s))) return rc;
   if ((rc = pqm.alloc((size_t)n * 2 * H * sizeof(float), s))) return rc;
   if ((rc = sbuf.alloc((size_t)n * H * sizeof(float), s))) return rc;
 
-  abs_partial_kernel<<<npart, 256, 0, s>>>(static_cast<const double*>(A->val), nnz, part.as<double>()); count_launch();
-  abs_final_kernel<<<1, 256, 0, s>>>(part.as<double>(), npart, nnz, normb.as<double>()); count_launch();
-  SPAI_CUDA(cudaGetLastError());
+  if ((rc = matrix_abs_mean(static_cast<const double*>(A->val), nnz, normb.as<double>(), s))) return rc;
 
   // tiles of rows for the edge passes
   TileSet et;

@@ -141,6 +141,8 @@ int sell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val
                 cudaStream_t s);
 // G and G^T values of a preconditioner in its pattern's SELL-32 layout
 int precond_sell(PrecondData& M, cudaStream_t s);
+// ||A|| = mean |A_ij| (Sec. 3.3) into out[0] (device), deterministic
+int matrix_abs_mean(const double* val, int64_t nnz, double* out, cudaStream_t s);
 int num_sms();
 
 // ---------------------------------------------------------------------------

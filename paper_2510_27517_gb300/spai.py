@@ -84,6 +84,7 @@ _SIGS = {
     "spai_ritz_extremes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]),
     "spai_ritz_kaporin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "spai_sai_loss": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "spai_build_pattern": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_pattern_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spai_pattern_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
@@ -304,6 +305,15 @@ def make_opts(rtol=1e-8, max_iter=0, replace_period=50, criterion=CRIT_RESIDUAL,
 def _host_f64(a):
     t = torch.as_tensor(a, dtype=torch.float64).cpu().contiguous()
     return t, C.c_void_p(t.data_ptr())
+
+
+def sai_loss(A: CSRMatrix, M: Precond, w: torch.Tensor, stream=None) -> torch.Tensor:
+    """SAI loss of every probe column of w (n x k float64 on the device, k <= 32)."""
+    assert w.dtype == torch.float64 and w.is_cuda and w.dim() == 2 and w.shape[0] == A.n
+    w = w.contiguous()
+    out = torch.empty(w.shape[1], dtype=torch.float64, device=w.device)
+    _check(lib().spai_sai_loss(C.byref(A._c()), M.h, _ptr(w), w.shape[1], _ptr(out), _stream(stream)))
+    return out
 
 
 def ritz_extremes(alpha, beta):
