@@ -553,6 +553,65 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_ppt(args):
+    """The paper's synthetic family A = P P^T + 1e-4 I (App. C: P of density
+    3e-4, n uniform in [12k, 24k], row-average node feature): a batch of
+    systems with GNN-built G solved together to rtol 1e-8 (float32 PCG in
+    float64 refinement), against the same systems solved one after another."""
+    import numpy as np
+    import torch
+
+    import paper_2510_27517_gb300 as spai
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    blob = W.gnn_random_weights(1, 4, seed=W.BASE_SEED + 100)
+    systems, preconds, bs, keep, sizes = [], [], [], [], []
+    for i, (n, seed) in enumerate(W.ppt_batch(args.batch)):
+        A_h = W.ppt_synthetic(n, seed=seed)
+        A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
+        P, M = _gnn_for(spai, A, A_h, W.row_average_feature(A_h).astype(np.float32), blob, 1, spai.F32, args.eps)
+        systems.append(spai.system_create(A)), preconds.append(M), keep.append((A, P))
+        bs.append(torch.tensor(W.rhs_uniform(A_h.n, W.BASE_SEED + 2000 + i), device="cuda"))
+        sizes.append((A_h.n, A_h.nnz))
+    xs = [torch.zeros_like(b) for b in bs]
+    kw = dict(precision=spai.PREC_MIXED, rtol=1e-8, max_iter=args.max_iter)
+
+    def batch():
+        for x in xs:
+            x.zero_()
+        return spai.pcg_solve_batched(systems, preconds, bs, xs, **kw)
+
+    for _ in range(args.warmup):
+        batch()
+    ts, res = [], None
+    for _ in range(args.steps):
+        res, ms = _timed(batch)
+        ts.append(ms)
+    bad = [r for r in res if r["status"] != 0 or not r["true_rel_res"] <= 1e-8]
+    if bad:
+        raise RuntimeError(f"{len(bad)} systems missed rtol 1e-8: {bad[:2]}")
+
+    def seq():
+        out = []
+        for S, M, b, x in zip(systems, preconds, bs, xs):
+            x.zero_()
+            out.append(spai.system_solve(S, M, b, x, **kw))
+        return out
+    _, alone_ms = _timed(seq)
+    ms = statistics.median(ts)
+    iters = [r["iters"] for r in res]
+    line = _common_line(args, "solves/s to rtol 1e-8 (synthetic P P^T + eps I batch)", args.batch / (ms / 1e3),
+                        "solves/s",
+                        {"workload": f"{args.batch} systems A = P P^T + 1e-4 I, n uniform [12000, 24000], P density "
+                                     f"3e-4, GNN-SPAI G (f32), eps {args.eps}, f32 PCG in f64 refinement",
+                         "sum_nnz": sum(z for _, z in sizes)},
+                        {"ms_per_batch": ms, "iters_min": min(iters), "iters_max": max(iters),
+                         "iters_mean": statistics.mean(iters), "one_at_a_time_ms": alone_ms,
+                         "batch_speedup": alone_ms / ms, "ms_per_solve_alone_mean": alone_ms / args.batch})
+    print(json.dumps(line))
+
+
 def run_serve(args):
     """Continuous-batching serving against the plain float64 one-at-a-time
     form on the same request trace.
@@ -757,7 +816,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic-per-iter", type=float, default=0.0,
                     help="DRAM bytes per inner iteration from an ncu capture of the current kernel")
-    ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "graph", "batch", "serve"])
+    ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "graph", "batch", "serve", "ppt"])
     ap.add_argument("--graph-n", type=int, default=1_000_000)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-side-hi", type=int, default=512)
@@ -788,6 +847,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "ppt":
+        run_ppt(args)
     else:
         run_ours(args)
 

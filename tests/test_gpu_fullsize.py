@@ -132,3 +132,30 @@ def test_aniso_batch_alone_equals_batch(spai_lib):
         assert rb["status"] == 0 and rb["iters"] == ra["iters"] and rb["outer_iters"] == ra["outer_iters"]
         assert torch.equal(xa, xb)
         assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, xb.cpu().numpy(), b.cpu().numpy()) <= 1e-8
+
+
+def test_paper_synthetic_ppt_gnn_and_solve(spai_lib):
+    # the paper's synthetic family A = P P^T + 1e-4 I (App. C), row-average
+    # node feature: pattern exact, G against the oracle, mixed solve to 1e-8
+    from oracle import pattern as Pt
+    spai = spai_lib
+    A = W.ppt_synthetic(3000, seed=W.BASE_SEED + 60)
+    dA = upload(spai, A)
+    P = spai.build_pattern(dA, spai.PATTERN_FULL)
+    out = {key: t.cpu().numpy() for key, t in P.export().items()}
+    trp, tci, perm = Pt.transpose_fast(A.n, A.rowptr, A.colidx)
+    assert np.array_equal(out["perm"], perm) and np.array_equal(out["t_colidx"], tci)
+    v = W.row_average_feature(A)
+    blob = W.gnn_random_weights(1, 4, seed=W.BASE_SEED + 100)
+    M = spai.gnn_precond(dA, P, torch.tensor(v.reshape(-1, 1).astype(np.float32), device="cuda"),
+                         torch.tensor(blob, device="cuda"), d_node=1, n_layers=4, g_dtype=spai.F32, eps=0.3)
+    g, _ = M.export(spai.F64)
+    ref = gnn.gnn_forward(A.n, A.rowptr, A.colidx, A.val, v, blob)
+    g = g.cpu().numpy()
+    assert np.abs(g - ref).max() <= TOL_G * np.abs(ref).max()
+    b = W.rhs_uniform(A.n, W.BASE_SEED + 61)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = spai.pcg_solve(dA, M, torch.tensor(b, device="cuda"), x, precision=spai.PREC_MIXED, rtol=1e-8,
+                       max_iter=200000)
+    assert r["status"] == 0
+    assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x.cpu().numpy(), b) <= 1e-8

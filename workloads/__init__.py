@@ -294,6 +294,29 @@ def random_spd_sparse(n: int, density: float, seed: int, diag_boost: float = 1.0
     return coo_to_csr(n, rows, cols, vals)
 
 
+def ppt_synthetic(n: int, density: float = 3e-4, eps: float = 1e-4, seed: int = BASE_SEED + 6) -> CSR:
+    """The paper's synthetic system A = P P^T + eps I (App. C): P is n x n
+    with density * n^2 entries at uniformly random distinct positions and
+    standard normal values; A has about 4x that density (1.2e-3 for the
+    paper's 3e-4) and is SPD for eps > 0."""
+    import scipy.sparse as sp
+    g = rng(seed)
+    m = max(1, int(round(density * n * n)))
+    keys = np.unique(g.integers(0, n * n, size=int(m * 1.05) + 8, dtype=np.int64))
+    keys = g.permutation(keys)[:m]
+    P = sp.csr_matrix((g.standard_normal(keys.size), (keys // n, keys % n)), shape=(n, n))
+    A = (P @ P.T + eps * sp.identity(n, format="csr")).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return CSR(n, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))
+
+
+def ppt_batch(count: int, seed: int = BASE_SEED + 7, n_lo: int = 12_000, n_hi: int = 24_000):
+    """Sizes and seeds of a batch of synthetic systems, n uniform in [n_lo, n_hi]."""
+    g = rng(seed)
+    return [(int(g.integers(n_lo, n_hi + 1)), int(g.integers(0, 2 ** 31))) for _ in range(count)]
+
+
 def random_dense_spd(n: int, seed: int, cond: float = 10.0) -> np.ndarray:
     """Dense SPD matrix with eigenvalues log-spaced in [1, cond]."""
     g = rng(seed)
