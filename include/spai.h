@@ -176,6 +176,12 @@ int spai_ritz_kaporin(const double* alpha, const double* beta, int64_t k, double
  * ------------------------------------------------------------------------ */
 int spai_sai_loss(const spai_csr* A, const spai_precond* M, const double* w, int32_t k, double* loss, void* stream);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): runs
+ * a kernel whose grid barrier and mbarrier can never complete, with a limit
+ * of limit_us microseconds (1..1e6).  *detected = 1 when both waits gave up,
+ * flagged SPAI_ERR_TIMEOUT and returned (the context stays usable). */
+int spai_selftest_wait_timeout(int64_t limit_us, int32_t* detected, void* stream);
+
 /* Fills `o` with the defaults (rtol 1e-8, replace_period 50, RESIDUAL, F64). */
 void spai_pcg_opts_default(spai_pcg_opts* o);
 

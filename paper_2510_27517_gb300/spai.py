@@ -85,6 +85,7 @@ _SIGS = {
                                      C.POINTER(C.c_double)]),
     "spai_ritz_kaporin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "spai_sai_loss": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "spai_selftest_wait_timeout": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.c_void_p]),
     "spai_build_pattern": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_pattern_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spai_pattern_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
@@ -314,6 +315,13 @@ def sai_loss(A: CSRMatrix, M: Precond, w: torch.Tensor, stream=None) -> torch.Te
     out = torch.empty(w.shape[1], dtype=torch.float64, device=w.device)
     _check(lib().spai_sai_loss(C.byref(A._c()), M.h, _ptr(w), w.shape[1], _ptr(out), _stream(stream)))
     return out
+
+
+def selftest_wait_timeout(limit_us=20000, stream=None) -> bool:
+    """True when the device-side bounded waits gave up and reported it."""
+    d = C.c_int32()
+    _check(lib().spai_selftest_wait_timeout(limit_us, C.byref(d), _stream(stream)))
+    return bool(d.value)
 
 
 def ritz_extremes(alpha, beta):

@@ -314,3 +314,15 @@ def test_lanczos_coefficients_and_condition_estimates(spai_lib):
     kap = spai.ritz_kaporin(al, be)
     assert 1.0 < kap < hi / lo
     assert kap == pytest.approx(spectrum.kappa_kaporin(lam), rel=0.25)
+
+
+def test_bounded_waits_time_out_and_context_survives(spai_lib):
+    # a grid barrier nobody releases and an mbarrier nothing arrives on give up
+    # after 20 ms with a timeout status; a solve afterwards still works
+    spai = spai_lib
+    assert spai.selftest_wait_timeout(20000)
+    A = W.poisson2d(16)
+    dA = upload(spai, A)
+    M, _ = fsai_precond(spai, A, dA)
+    res, x, _ = gpu_solve(spai, dA, M, W.rhs_uniform(A.n, 3))
+    assert res["status"] == 0
