@@ -301,7 +301,8 @@ def run_ours(args):
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     traffic = None
-    if args.traffic_per_iter > 0:
+    # the capture's figure holds for the captured configuration only
+    if args.traffic_per_iter > 0 and args.grid == 128 and args.gdtype == "f32" and prec == spai.PREC_MIXED:
         iters_per_launch = sum(r["iters"] for r in timed) / max(1, sum(r["launches"] for r in timed))
         traffic = args.traffic_per_iter * iters_per_launch
 
@@ -814,7 +815,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=400000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--traffic-per-iter", type=float, default=0.0,
+    # DRAM bytes per inner iteration of the current persistent kernel at 128^3 from its ncu capture
+    # (profiles/engine_kernel_diffusion3d_128.md: 13.54 GB for 30 iterations plus the float64 start and
+    # one refinement, about 0.85 GB); 0 reports null
+    ap.add_argument("--traffic-per-iter", type=float, default=4.23e8,
                     help="DRAM bytes per inner iteration from an ncu capture of the current kernel")
     ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "graph", "batch", "serve", "ppt"])
     ap.add_argument("--graph-n", type=int, default=1_000_000)
