@@ -140,6 +140,7 @@ constexpr int kStages = 4;    // largest ring (shared-memory arrays)
 constexpr int kMaxK = 64;     // groups per work item at most
 constexpr int kWarpE = 256;   // entries per warp product chunk
 constexpr int kAlignE = 8;    // bulk copies start at multiples of 8 entries (16 B for every type)
+constexpr int kSlicesInReg = 63;  // SELL groups of up to this many slices keep their offsets in registers
 
 // y_row = sum over the row's entries of val * op.gather(col), in stored
 // order, then op.fin(row, y_row, op.pre(row)).  Rows are processed in groups
@@ -503,35 +504,46 @@ __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict_
     const uint32_t c = c0 + k;
     const int st = (int)(c % NS);
     const unsigned parity = (c / NS) & 1u;
+    // slice offsets of the group, loaded before the wait (the group's slice
+    // range is known from the item): lane l holds sptr[first + l] and
+    // sptr[first + 32 + l]
+    const int gs0 = P.grow[k];
+    const int nsl = P.grow[k + 1] - gs0;
+    const int so0 = lane <= nsl ? __ldg(sptr + gs0 + lane) : 0;
+    const int so1 = lane + 32 <= nsl ? __ldg(sptr + gs0 + 32 + lane) : 0;
     if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
     const GroupHdr h = P.hdr[st];
     const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
     const int32_t* cs = reinterpret_cast<const int32_t*>(base) - h.e0a;
     const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) - h.e0a;
-    const int nsl = h.re - h.r;
     int j = (int)((uint32_t)(warp - (int)(blocks % NW) + NW) % NW);
     for (; j < nsl; j += NW) {
-      const int sl = h.r + j;
-      const int off = __ldg(sptr + sl);
-      const int w = (__ldg(sptr + sl + 1) - off) >> 5;
+      const int sl = gs0 + j;
+      int off, end;
+      if (nsl <= kSlicesInReg) {
+        off = __shfl_sync(0xffffffffu, j < 32 ? so0 : so1, j & 31);
+        end = __shfl_sync(0xffffffffu, j + 1 < 32 ? so0 : so1, (j + 1) & 31);
+      } else {
+        off = __ldg(sptr + sl);
+        end = __ldg(sptr + sl + 1);
+      }
+      const int w = (end - off) >> 5;
       const int row = sl * 32 + lane;
       const bool valid = row < n;
-      int len = 0;
       typename Op::Pre pr;
-      if (valid) {
-        len = __ldg(rp + row + 1) - __ldg(rp + row);
-        pr = op.pre(row);
-      }
+      if (valid) pr = op.pre(row);
+      // padding entries (beyond a row's length) hold column 0 and value 0:
+      // they add exact zeros, so no row lengths are needed
       const int32_t* cl = cs + off + lane;
       const MV* vl = vs + off + lane;
       AT acc = AT(0);
       for (int k0 = 0; k0 < w; k0 += kB) {
         AT gv[kB];  // all gathers of the batch in flight before the sums
 #pragma unroll
-        for (int u = 0; u < kB; ++u) gv[u] = (k0 + u < len) ? op.gather(cl[32 * (k0 + u)]) : AT(0);
+        for (int u = 0; u < kB; ++u) gv[u] = (k0 + u < w) ? op.gather(cl[32 * (k0 + u)]) : AT(0);
 #pragma unroll
         for (int u = 0; u < kB; ++u)
-          if (k0 + u < len) acc = rfma(Conv<AT>::f(vl[32 * (k0 + u)]), gv[u], acc);
+          if (k0 + u < w) acc = rfma(Conv<AT>::f(vl[32 * (k0 + u)]), gv[u], acc);
       }
       if (valid) op.fin(row, acc, pr, p0, p1);
     }
