@@ -121,3 +121,48 @@ def test_locality_ball_reproduces_full_forward(L):
             assert err <= 1e-13, err
         else:
             assert err > 1e-9, err
+
+
+def test_blocks_of_size_one_are_the_scalar_forward():
+    A, k = W.diffusion3d(5)
+    v = W.diffusion3d_node_features(k)
+    blob = W.gnn_random_weights(4, 2)
+    g1 = gnn.gnn_forward(A.n, A.rowptr, A.colidx, A.val, v, blob, n_layers=2)
+    gb = gnn.gnn_forward_blocks(A.n, A.rowptr, A.colidx, A.val, v, blob, 1, n_layers=2)
+    assert np.array_equal(g1, gb)
+
+
+def test_block_parameter_count_and_constant_decoder():
+    # 3 x 3 blocks: E_e takes 9 inputs and D writes 9 outputs
+    assert W.gnn_param_count(4, 4, b=3) == 720 + (9 * 24 + 24 + 576 + 24) + 4 * (2352 + 1200 + 2352) + (576 + 24 + 9 * 24 + 9)
+    A, feat = W.elastic3d(3)
+    blob = np.zeros(W.gnn_param_count(4, 2, b=3))
+    c = np.arange(1.0, 10.0)
+    blob[-9:] = c                       # decoder output bias: every block of G is reshape(c)
+    g = gnn.gnn_forward_blocks(A.n, A.rowptr, A.colidx, A.val, feat, blob, 3, n_layers=2)
+    nb, browptr, bcol, bval = gnn.block_graph(A.n, A.rowptr, A.colidx, A.val, 3)
+    want = gnn.blocks_to_csr_values(A.n, A.rowptr, browptr, np.tile(c.reshape(1, 3, 3), (bcol.size, 1, 1)), 3)
+    assert np.array_equal(g, want)
+
+
+def test_block_graph_round_trip_and_equivariance():
+    A, feat = W.elastic3d(3)
+    nb, browptr, bcol, bval = gnn.block_graph(A.n, A.rowptr, A.colidx, A.val, 3)
+    assert nb == 27 and np.array_equal(gnn.blocks_to_csr_values(A.n, A.rowptr, browptr, bval, 3), A.val)
+    # relabelling the nodes relabels the blocks of G
+    blob = W.gnn_random_weights(4, 2, b=3)
+    g = gnn.gnn_forward_blocks(A.n, A.rowptr, A.colidx, A.val, feat, blob, 3, n_layers=2)
+    perm = np.random.default_rng(2).permutation(nb)          # new node p holds old node perm[p]
+    inv = np.argsort(perm)
+    brow = np.repeat(np.arange(nb), np.diff(browptr))
+    nrow, ncol = inv[brow], inv[bcol]                         # new labels of every block
+    rows = np.concatenate([3 * nrow + r for r in range(3) for c in range(3)])
+    cols = np.concatenate([3 * ncol + c for r in range(3) for c in range(3)])
+    vals = np.concatenate([bval[:, r, c] for r in range(3) for c in range(3)])
+    Ap = W.coo_to_csr(A.n, rows, cols, vals)                   # dense blocks, zeros kept
+    assert Ap.nnz == A.nnz
+    gp = gnn.gnn_forward_blocks(Ap.n, Ap.rowptr, Ap.colidx, Ap.val, feat[perm], blob, 3, n_layers=2)
+    sp = (3 * perm[:, None] + np.arange(3)).ravel()           # old scalar index of every new row
+    G = W.CSR(A.n, A.rowptr, A.colidx, g).to_dense()
+    Gp = W.CSR(Ap.n, Ap.rowptr, Ap.colidx, gp).to_dense()
+    assert np.allclose(Gp, G[np.ix_(sp, sp)], rtol=1e-12, atol=1e-12)

@@ -294,6 +294,63 @@ def random_spd_sparse(n: int, density: float, seed: int, diag_boost: float = 1.0
     return coo_to_csr(n, rows, cols, vals)
 
 
+def elastic3d(N: int, seed: int = BASE_SEED + 8, shift: float = 1e-3):
+    """Block-sparse SPD system with 3 x 3 blocks on an N^3 node grid (the
+    shape of the paper's hyperelastic systems: 3 unknowns per node, App. C).
+
+    Every grid edge (i, j) with unit direction n_ij and a log-normal weight
+    k_ij adds k_ij (e_i - e_j)(e_i - e_j)^T (x) B_ij, B_ij = I + n n^T
+    (a spring that is stiffer along the edge), plus shift * mean(diag) on the
+    diagonal; SPD.  Returns the scalar CSR of size 3 N^3 with dense 3 x 3
+    blocks (each block row's three scalar rows list the same blocks in column
+    order, 3 entries per block), and the node features: position in
+    [-1, 1]^3 and a boundary flag (d_node = 4, as the paper's input: position
+    and a one-hot Dirichlet indicator)."""
+    g = rng(seed)
+    nn = N ** 3
+    idx = np.arange(nn).reshape(N, N, N)
+    blocks = {}
+    def add(i, j, M):
+        key = (int(i), int(j))
+        blocks[key] = blocks.get(key, 0) + M
+    diag = np.zeros((nn, 3, 3))
+    for ax in range(3):
+        sl_a = [slice(None)] * 3
+        sl_b = [slice(None)] * 3
+        sl_a[ax] = slice(0, N - 1)
+        sl_b[ax] = slice(1, N)
+        a = idx[tuple(sl_a)].ravel()
+        b = idx[tuple(sl_b)].ravel()
+        k = np.exp(0.5 * g.standard_normal(a.size))
+        B = np.eye(3)
+        B[ax, ax] += 1.0
+        for ii, jj, kk in zip(a, b, k):
+            M = kk * B
+            diag[ii] += M
+            diag[jj] += M
+            add(ii, jj, -M)
+            add(jj, ii, -M)
+    dmean = np.mean(np.einsum("ikk->ik", diag))
+    for i in range(nn):
+        add(i, i, diag[i] + shift * dmean * np.eye(3))
+    keys = sorted(blocks)
+    brow = np.array([k[0] for k in keys])
+    bcol = np.array([k[1] for k in keys])
+    bval = np.array([blocks[k] for k in keys])          # (nnzb, 3, 3)
+    rows, cols, vals = [], [], []
+    for r in range(3):
+        for c in range(3):
+            rows.append(3 * brow + r)
+            cols.append(3 * bcol + c)
+            vals.append(bval[:, r, c])
+    A = coo_to_csr(3 * nn, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    t = np.linspace(-1.0, 1.0, N)
+    X, Y, Z = np.meshgrid(t, t, t, indexing="ij")
+    bnd = ((idx == idx) & ((np.abs(X) == 1) | (np.abs(Y) == 1) | (np.abs(Z) == 1))).astype(np.float64)
+    feat = np.stack([X.ravel(), Y.ravel(), Z.ravel(), bnd.ravel()], axis=1).astype(np.float32)
+    return A, feat
+
+
 def ppt_synthetic(n: int, density: float = 3e-4, eps: float = 1e-4, seed: int = BASE_SEED + 6) -> CSR:
     """The paper's synthetic system A = P P^T + eps I (App. C): P is n x n
     with density * n^2 entries at uniformly random distinct positions and
@@ -355,25 +412,26 @@ def gnn_layer_shapes(d_node: int, n_layers: int, msg_raw_edge: bool = False, d_e
     return shapes
 
 
-def gnn_param_count(d_node: int, n_layers: int, msg_raw_edge: bool = False) -> int:
+def gnn_param_count(d_node: int, n_layers: int, msg_raw_edge: bool = False, b: int = 1) -> int:
     tot = 0
-    for _, fi, fo in gnn_layer_shapes(d_node, n_layers, msg_raw_edge):
+    for _, fi, fo in gnn_layer_shapes(d_node, n_layers, msg_raw_edge, d_edge=b * b, b=b):
         tot += HIDDEN * fi + HIDDEN + fo * HIDDEN + fo
     return tot
 
 
 def gnn_random_weights(d_node: int, n_layers: int = 4, seed: int = BASE_SEED + 100,
-                       msg_raw_edge: bool = False) -> np.ndarray:
+                       msg_raw_edge: bool = False, b: int = 1) -> np.ndarray:
     """Flat float32 weight blob with seeded U(-1/sqrt(fan_in), 1/sqrt(fan_in))
     initialisation of every weight and bias.
 
     Per MLP the layout is [W1 (24 x fan_in, row-major), b1 (24),
     W2 (fan_out x 24, row-major), b2 (fan_out)]; MLPs in the order of
-    gnn_layer_shapes.
+    gnn_layer_shapes; b x b blocks make the edge input and the decoder
+    output b^2 wide.
     """
     g = rng(seed)
     parts = []
-    for _, fi, fo in gnn_layer_shapes(d_node, n_layers, msg_raw_edge):
+    for _, fi, fo in gnn_layer_shapes(d_node, n_layers, msg_raw_edge, d_edge=b * b, b=b):
         a1 = 1.0 / math.sqrt(fi)
         parts.append(g.uniform(-a1, a1, size=HIDDEN * fi))
         parts.append(g.uniform(-a1, a1, size=HIDDEN))
