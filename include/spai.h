@@ -95,14 +95,16 @@ typedef struct spai_server spai_server;
  * float32 holding, for every MLP in the order E_n, E_e, (f_m, f_v, f_e) per
  * layer, D, the block [W1 (24 x fan_in, row-major), b1 (24), W2 (fan_out x 24,
  * row-major), b2 (fan_out)].  Every MLP is Linear -> ReLU -> Linear with 24
- * hidden units.  Fan-ins: E_n d_node, E_e 1, f_m 72 (or 49 with
- * SPAI_MSG_RAW), f_v 24, f_e 72, D 24; fan-outs 24 except D (1). */
+ * hidden units.  Fan-ins: E_n d_node, E_e b^2, f_m 72 (or 48 + b^2 with
+ * SPAI_MSG_RAW), f_v 24, f_e 72, D 24; fan-outs 24 except D (b^2), b the
+ * block size (1, or 3 for the paper's 3 x 3 blocks). */
 typedef struct {
   const float* blob;   /* device */
   int64_t count;       /* number of floats in blob (checked) */
   int32_t d_node;      /* node feature width, 1..16 */
   int32_t n_layers;    /* message-passing layers L, 0..8 (paper: 4) */
   int32_t msg_edge;    /* SPAI_MSG_LATENT or SPAI_MSG_RAW */
+  int32_t block;       /* b: 1 (0 is read as 1) or 3 */
 } spai_gnn_weights;
 
 typedef struct {
@@ -223,6 +225,14 @@ void spai_pattern_destroy(spai_pattern* P);
  * G is stored in `g_dtype` (F64, F32, BF16 or F16) together with G^T, and
  * eps is the shift of Eq. 1.  Returns SPAI_ERR_SHAPE on a d_node / weight /
  * pattern mismatch.
+ * Block form (W->block = b = 3, the paper's 3-unknowns-per-node systems):
+ * A is the scalar CSR of a matrix made of dense b x b blocks (each block
+ * row's b scalar rows list the same blocks in column order, b entries per
+ * block; SPAI_ERR_BAD_CSR otherwise).  The GNN runs on the node graph
+ * (n / b nodes, node_feat is (n / b) x d_node), every edge feature is the
+ * block of A / ||A|| flattened row-major (||A|| over all stored scalar
+ * entries) and the decoder writes one b x b block of G per edge, stored
+ * in G's scalar CSR (A's pattern).
  * ------------------------------------------------------------------------ */
 int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const float* node_feat,
                      const spai_gnn_weights* W, int32_t g_dtype, double eps,

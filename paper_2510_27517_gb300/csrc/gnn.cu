@@ -23,6 +23,9 @@
 #include <cstring>
 #include <vector>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "internal.cuh"
 #include "gnn_tc.cuh"
 
@@ -37,9 +40,12 @@ constexpr int H = 24;        // hidden width d (Sec. 4.1)
 constexpr int MAXD = 16;     // largest node feature width accepted
 constexpr int ECAP = 256;    // edges staged per group (= block size)
 
+constexpr int BMAX = 3;      // largest block size b (edge feature and decoder output b^2 wide)
+constexpr int B2MAX = BMAX * BMAX;
+
 struct EdgeParams {
-  // encoder E_e (first pass only)
-  float W1ee[H];
+  // encoder E_e (first pass only): W1ee is 24 x b^2
+  float W1ee[H * B2MAX];
   float b1ee[H];
   float W2ee[H * H];
   float b2ee[H];
@@ -47,13 +53,13 @@ struct EdgeParams {
   float W1ec[H * H];
   float W2e[H * H];
   float b2e[H];
-  // first layer of the next f_m on the edge input (latent: 24x24, raw: 24x1)
+  // first layer of the next f_m on the edge input (latent: 24x24, raw: 24 x b^2)
   float W1mc[H * H];
-  // decoder D
+  // decoder D: 24 -> 24 -> b^2
   float W1d[H * H];
   float b1d[H];
-  float W2d[H];
-  float b2d;
+  float W2d[B2MAX * H];
+  float b2d[B2MAX];
 };
 
 struct EdgeArgs {
@@ -72,6 +78,10 @@ struct EdgeArgs {
   void* gt_out;             // G^T values (scattered through perm)
   const int32_t* perm;
   int gtype;
+  // b x b blocks: the graph above is the node graph; bval holds every block of
+  // A / ||A|| (row-major), srp the scalar row pointers G is written through
+  const float* bval;
+  const int32_t* srp;
 };
 
 __device__ __forceinline__ float* hptr(float* h, int64_t e, int c) {
@@ -96,8 +106,9 @@ __device__ __forceinline__ void store_g(void* out, int gtype, int64_t i, float v
   }
 }
 
-template <bool FIRST, bool LAST, bool MSG, bool RAW>
+template <bool FIRST, bool LAST, bool MSG, bool RAW, int B>
 __global__ void __launch_bounds__(ECAP) edge_kernel(const EdgeArgs a, const __grid_constant__ EdgeParams w) {
+  constexpr int B2 = B * B;
   __shared__ float zbuf[H][ECAP];
   __shared__ float racc[H];
   const double norm = *a.anorm;
@@ -128,12 +139,23 @@ __global__ void __launch_bounds__(ECAP) edge_kernel(const EdgeArgs a, const __gr
           }
           const int i = rl;
           const int j = __ldg(a.ci + e);
-          const float ev = (float)(__ldg(a.aval + e) / norm);
+          float ev[B2];
+          if (B == 1) {
+            ev[0] = (float)(__ldg(a.aval + e) / norm);
+          } else {
+#pragma unroll
+            for (int q = 0; q < B2; ++q) ev[q] = __ldg(a.bval + e * B2 + q);
+          }
           float h[H];
           if (FIRST) {
             float u[H];
 #pragma unroll
-            for (int o = 0; o < H; ++o) u[o] = fmaxf(fmaf(w.W1ee[o], ev, w.b1ee[o]), 0.f);
+            for (int o = 0; o < H; ++o) {
+              float acc = w.b1ee[o];
+#pragma unroll
+              for (int q = 0; q < B2; ++q) acc = fmaf(w.W1ee[o * B2 + q], ev[q], acc);
+              u[o] = fmaxf(acc, 0.f);
+            }
 #pragma unroll
             for (int o = 0; o < H; ++o) {
               float acc = 0.f;
@@ -174,7 +196,8 @@ __global__ void __launch_bounds__(ECAP) edge_kernel(const EdgeArgs a, const __gr
             for (int o = 0; o < H; ++o) {
               float acc = 0.f;
               if (RAW) {
-                acc = w.W1mc[o] * ev;
+#pragma unroll
+                for (int q = 0; q < B2; ++q) acc = fmaf(w.W1mc[o * B2 + q], ev[q], acc);
               } else {
 #pragma unroll
                 for (int q = 0; q < H; ++q) acc = fmaf(w.W1mc[o * H + q], h[q], acc);
@@ -183,17 +206,44 @@ __global__ void __launch_bounds__(ECAP) edge_kernel(const EdgeArgs a, const __gr
             }
           }
           if (LAST) {
-            float g = 0.f;
+            if (B == 1) {
+              float g = 0.f;
 #pragma unroll
-            for (int o = 0; o < H; ++o) {
-              float acc = 0.f;
+              for (int o = 0; o < H; ++o) {
+                float acc = 0.f;
 #pragma unroll
-              for (int q = 0; q < H; ++q) acc = fmaf(w.W1d[o * H + q], h[q], acc);
-              g = fmaf(w.W2d[o], fmaxf(acc + w.b1d[o], 0.f), g);
+                for (int q = 0; q < H; ++q) acc = fmaf(w.W1d[o * H + q], h[q], acc);
+                g = fmaf(w.W2d[o], fmaxf(acc + w.b1d[o], 0.f), g);
+              }
+              g = g + w.b2d[0];
+              store_g(a.g_out, a.gtype, e, g);
+              store_g(a.gt_out, a.gtype, __ldg(a.perm + e), g);
+            } else {
+              float hid[H];
+#pragma unroll
+              for (int o = 0; o < H; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < H; ++q) acc = fmaf(w.W1d[o * H + q], h[q], acc);
+                hid[o] = fmaxf(acc + w.b1d[o], 0.f);
+              }
+              // block e = (block row i, its k-th block): entry (r, c) of G's block
+              // sits at scalar position srp[B i + r] + B k + c
+              const int64_t k = e - __ldg(a.rp + i);
+#pragma unroll
+              for (int r = 0; r < B; ++r) {
+                const int64_t base = __ldg(a.srp + (int64_t)B * i + r) + (int64_t)B * k;
+#pragma unroll
+                for (int c = 0; c < B; ++c) {
+                  float g = 0.f;
+#pragma unroll
+                  for (int o = 0; o < H; ++o) g = fmaf(w.W2d[(r * B + c) * H + o], hid[o], g);
+                  g = g + w.b2d[r * B + c];
+                  store_g(a.g_out, a.gtype, base + c, g);
+                  store_g(a.gt_out, a.gtype, __ldg(a.perm + base + c), g);
+                }
+              }
             }
-            g = g + w.b2d;
-            store_g(a.g_out, a.gtype, e, g);
-            store_g(a.gt_out, a.gtype, __ldg(a.perm + e), g);
           }
         }
         if (MSG) {
@@ -528,6 +578,41 @@ struct MLPView {
 
 }  // namespace
 
+namespace {
+// Node graph of a scalar CSR made of dense b x b blocks: one thread per block
+// row checks that its b scalar rows list the same aligned blocks, and writes
+// the block row pointers, block columns and the blocks of A / ||A||.
+__global__ void block_graph_kernel(const int32_t* __restrict__ srp, const int32_t* __restrict__ sci,
+                                   const double* __restrict__ sval, int64_t nb, int b, const double* __restrict__ norm,
+                                   int32_t* browptr, int32_t* bcol, float* bval, int* bad) {
+  const double inv = 1.0 / norm[0];
+  const int b2 = b * b;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = (int64_t)b * i;
+    const int len = srp[r0 + 1] - srp[r0];
+    if (len % b != 0 || srp[r0] % b2 != 0) { atomicOr(bad, 1); continue; }
+    bool ok = true;
+    for (int r = 1; r < b; ++r) ok = ok && (srp[r0 + r + 1] - srp[r0 + r] == len);
+    if (!ok) { atomicOr(bad, 1); continue; }
+    const int nblk = len / b;
+    const int64_t k0 = srp[r0] / b2;
+    browptr[i] = (int32_t)k0;
+    if (i == nb - 1) browptr[nb] = (int32_t)(k0 + nblk);
+    for (int q = 0; q < nblk; ++q) {
+      const int c0 = sci[srp[r0] + b * q];
+      if (c0 % b != 0) { atomicOr(bad, 1); break; }
+      bcol[k0 + q] = c0 / b;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) {
+          const int64_t pos = srp[r0 + r] + (int64_t)b * q + c;
+          if (sci[pos] != c0 + c) atomicOr(bad, 1);
+          bval[(k0 + q) * b2 + r * b + c] = (float)(sval[pos] * inv);
+        }
+    }
+  }
+}
+}  // namespace
+
 // ||A|| (Sec. 3.3) into out[0] on the device; the same deterministic sum
 // everywhere it is needed.
 int matrix_abs_mean(const double* val, int64_t nnz, double* out, cudaStream_t s) {
@@ -552,18 +637,22 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   if (W->n_layers < 0 || W->n_layers > 8) return set_error(SPAI_ERR_SHAPE, "n_layers must be in 0..8");
   if (W->msg_edge != SPAI_MSG_LATENT && W->msg_edge != SPAI_MSG_RAW) return set_error(SPAI_ERR_INVALID, "msg_edge");
   if (!dtype_size(g_dtype)) return set_error(SPAI_ERR_INVALID, "unknown G dtype");
+  const int bs = W->block <= 0 ? 1 : W->block;
+  if (bs != 1 && bs != BMAX) return set_error(SPAI_ERR_INVALID, "block size must be 1 or %d", BMAX);
+  if (A->n % bs != 0) return set_error(SPAI_ERR_SHAPE, "n is not a multiple of the block size");
+  const int b2 = bs * bs;
   const bool raw = W->msg_edge == SPAI_MSG_RAW;
   const int L = W->n_layers, dn = W->d_node;
-  // layout
+  // layout (edge feature and decoder output b^2 wide)
   std::vector<std::pair<int, int>> shapes;
   shapes.push_back({dn, H});
-  shapes.push_back({1, H});
+  shapes.push_back({b2, H});
   for (int t = 0; t < L; ++t) {
-    shapes.push_back({2 * H + (raw ? 1 : H), H});
+    shapes.push_back({2 * H + (raw ? b2 : H), H});
     shapes.push_back({H, H});
     shapes.push_back({3 * H, H});
   }
-  shapes.push_back({H, 1});
+  shapes.push_back({H, b2});
   int64_t need = 0;
   for (auto& sh : shapes) need += (int64_t)H * sh.first + H + (int64_t)sh.second * H + sh.second;
   if (W->count != need)
@@ -597,15 +686,16 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
       for (int q = 0; q < ncol; ++q) dst[o * ncol + q] = v.W1[o * v.fi + 2 * H + q];
   };
 
-  const int64_t n = A->n, nnz = A->nnz;
+  const int64_t ns = A->n, nnzs = A->nnz;     // scalar sizes (G's values)
+  const int64_t n = ns / bs, nnz = nnzs / b2;   // the GNN's graph: nodes and edges (blocks)
   int rc;
   auto Pre = std::make_shared<PrecondData>();
   Pre->P = P;
   Pre->gtype = g_dtype;
   Pre->eps = eps;
   const size_t es = dtype_size(g_dtype);
-  if ((rc = Pre->g_val.alloc((nnz + 16) * es, s))) return rc;
-  if ((rc = Pre->gt_val.alloc((nnz + 16) * es, s))) return rc;
+  if ((rc = Pre->g_val.alloc((nnzs + 16) * es, s))) return rc;
+  if ((rc = Pre->gt_val.alloc((nnzs + 16) * es, s))) return rc;
   Pre->g_val.keep();
   Pre->gt_val.keep();
 
@@ -619,11 +709,37 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   if ((rc = pqm.alloc((size_t)n * 2 * H * sizeof(float), s))) return rc;
   if ((rc = sbuf.alloc((size_t)n * H * sizeof(float), s))) return rc;
 
-  if ((rc = matrix_abs_mean(static_cast<const double*>(A->val), nnz, normb.as<double>(), s))) return rc;
+  if ((rc = matrix_abs_mean(static_cast<const double*>(A->val), nnzs, normb.as<double>(), s))) return rc;
+
+  // the graph of the GNN: A's own pattern, or the node graph of its b x b blocks
+  const int32_t* grp = P->g_rp();
+  const int32_t* gci = P->g_ci();
+  DevMem brp, bci, bvl;
+  if (bs > 1) {
+    DevMem bad;
+    if ((rc = brp.alloc((n + 1 + 16) * sizeof(int32_t), s))) return rc;
+    if ((rc = bci.alloc((nnz + 16) * sizeof(int32_t), s))) return rc;
+    if ((rc = bvl.alloc((nnz * b2 + 16) * sizeof(float), s))) return rc;
+    if ((rc = bad.alloc(sizeof(int), s))) return rc;
+    SPAI_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    SPAI_CUDA(cudaMemsetAsync(brp.p, 0, (n + 1 + 16) * sizeof(int32_t), s));
+    const int bgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+    block_graph_kernel<<<bgrid > 0 ? bgrid : 1, 256, 0, s>>>(P->g_rp(), P->g_ci(), static_cast<const double*>(A->val),
+                                                             n, bs, normb.as<double>(), brp.as<int32_t>(),
+                                                             bci.as<int32_t>(), bvl.as<float>(), bad.as<int>());
+    count_launch();
+    SPAI_CUDA(cudaGetLastError());
+    int hbad = 0;
+    SPAI_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return set_error(SPAI_ERR_BAD_CSR, "A is not made of dense %d x %d blocks", bs, bs);
+    grp = brp.as<int32_t>();
+    gci = bci.as<int32_t>();
+  }
 
   // tiles of rows for the edge passes
   TileSet et;
-  if ((rc = build_tiles(P->g_rp(), n, nnz, 2048, et, s))) return rc;
+  if ((rc = build_tiles(grp, n, nnz, 2048, et, s))) return rc;
 
   // ---- tensor-core node kernels: launch configuration and weight blobs ----
   const int64_t ntiles = (n + tc::kM - 1) / tc::kM;
@@ -670,9 +786,11 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   }
   EdgeArgs ea;
   memset(&ea, 0, sizeof(ea));
-  ea.rp = P->g_rp();
-  ea.ci = P->g_ci();
+  ea.rp = grp;
+  ea.ci = gci;
   ea.aval = static_cast<const double*>(A->val);
+  ea.bval = bvl.as<float>();
+  ea.srp = P->g_rp();
   ea.anorm = normb.as<double>();
   ea.tiles = et.starts.as<int32_t>();
   ea.ntiles = et.ntiles;
@@ -690,28 +808,43 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
   auto fill_decoder = [&](EdgeParams& p) {
     memcpy(p.W1d, Dd.W1, sizeof(p.W1d));
     memcpy(p.b1d, Dd.b1, sizeof(p.b1d));
-    memcpy(p.W2d, Dd.W2, sizeof(p.W2d));
-    p.b2d = Dd.b2[0];
+    memcpy(p.W2d, Dd.W2, sizeof(float) * b2 * H);
+    memcpy(p.b2d, Dd.b2, sizeof(float) * b2);
   };
   auto fill_msg = [&](EdgeParams& p, int t) {
-    if (raw) edge_cols(fm(t), p.W1mc, 1);
+    if (raw) edge_cols(fm(t), p.W1mc, b2);
     else edge_cols(fm(t), p.W1mc, H);
   };
+  // one edge pass, instantiated for the block size
+  auto edge_pass = [&](auto first, auto last, auto msg, auto rawc, const EdgeParams& p) -> int {
+    constexpr bool F = decltype(first)::value, La = decltype(last)::value, Mg = decltype(msg)::value,
+                   Rw = decltype(rawc)::value;
+    if (bs == 1) edge_kernel<F, La, Mg, Rw, 1><<<egrid, ECAP, 0, s>>>(ea, p);
+    else edge_kernel<F, La, Mg, Rw, BMAX><<<egrid, ECAP, 0, s>>>(ea, p);
+    count_launch();
+    SPAI_CUDA(cudaGetLastError());
+    return SPAI_OK;
+  };
+  using T = std::true_type;
+  using Fl = std::false_type;
   {
     // pass 0: E_e, then the first message (or the decoder when L == 0)
     EdgeParams p;
     memset(&p, 0, sizeof(p));
-    for (int o = 0; o < H; ++o) { p.W1ee[o] = Ee.W1[o]; p.b1ee[o] = Ee.b1[o]; p.b2ee[o] = Ee.b2[o]; }
+    for (int o = 0; o < H; ++o) {
+      for (int q = 0; q < b2; ++q) p.W1ee[o * b2 + q] = Ee.W1[o * b2 + q];
+      p.b1ee[o] = Ee.b1[o];
+      p.b2ee[o] = Ee.b2[o];
+    }
     memcpy(p.W2ee, Ee.W2, sizeof(p.W2ee));
     if (L == 0) {
       fill_decoder(p);
-      edge_kernel<true, true, false, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch();
+      rc = edge_pass(T{}, T{}, Fl{}, Fl{}, p);
     } else {
       fill_msg(p, 0);
-      if (raw) { edge_kernel<true, false, true, true><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
-      else { edge_kernel<true, false, true, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
+      rc = raw ? edge_pass(T{}, Fl{}, T{}, T{}, p) : edge_pass(T{}, Fl{}, T{}, Fl{}, p);
     }
-    SPAI_CUDA(cudaGetLastError());
+    if (rc) return rc;
   }
   for (int t = 0; t < L; ++t) {
     {
@@ -740,7 +873,7 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
       tb.add(r, H, bias);
       tb.p.has_m = has_m;
       DevMem lblob;
-      if ((rc = launch_tc(node_layer_tc_kernel, tb, lblob, P->g_rp(), n, (const float*)sbuf.as<float>(),
+      if ((rc = launch_tc(node_layer_tc_kernel, tb, lblob, grp, n, (const float*)sbuf.as<float>(),
                           xbuf.as<float>(), pqe.as<float>(), pqm.as<float>())))
         return rc;
     }
@@ -752,13 +885,12 @@ int gnn_forward(const spai_csr* A, const std::shared_ptr<PatternData>& P, const 
     memcpy(p.b2e, e.b2, sizeof(p.b2e));
     if (t + 1 == L) {
       fill_decoder(p);
-      edge_kernel<false, true, false, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch();
+      rc = edge_pass(Fl{}, T{}, Fl{}, Fl{}, p);
     } else {
       fill_msg(p, t + 1);
-      if (raw) { edge_kernel<false, false, true, true><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
-      else { edge_kernel<false, false, true, false><<<egrid, ECAP, 0, s>>>(ea, p); count_launch(); }
+      rc = raw ? edge_pass(Fl{}, Fl{}, T{}, T{}, p) : edge_pass(Fl{}, Fl{}, T{}, Fl{}, p);
     }
-    SPAI_CUDA(cudaGetLastError());
+    if (rc) return rc;
   }
   double hn = 0.0;
   int herr = 0;

@@ -40,7 +40,7 @@ class _CSR(C.Structure):
 
 class _GNNW(C.Structure):
     _fields_ = [("blob", C.c_void_p), ("count", C.c_int64), ("d_node", C.c_int32), ("n_layers", C.c_int32),
-                ("msg_edge", C.c_int32)]
+                ("msg_edge", C.c_int32), ("block", C.c_int32)]
 
 
 class _Opts(C.Structure):
@@ -263,10 +263,11 @@ def build_pattern(A: CSRMatrix, kind=PATTERN_FULL, stream=None) -> Pattern:
 
 
 def gnn_precond(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.Tensor, d_node: int,
-                n_layers: int = 4, msg_edge=MSG_LATENT, g_dtype=F32, eps=1e-4, stream=None) -> Precond:
+                n_layers: int = 4, msg_edge=MSG_LATENT, g_dtype=F32, eps=1e-4, block=1, stream=None) -> Precond:
+    """block=3: A made of dense 3 x 3 blocks, node_feat one row per block row."""
     assert node_feat.dtype == torch.float32 and node_feat.is_contiguous()
     assert blob.dtype == torch.float32 and blob.is_contiguous()
-    w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge)
+    w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge, block)
     h = C.c_void_p()
     _check(lib().spai_gnn_precond(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), g_dtype, float(eps),
                                   C.byref(h), _stream(stream)))

@@ -114,3 +114,42 @@ def test_gnn_then_mixed_solve(spai_lib):
     from oracle import pcg
     assert res["status"] == 0
     assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x.cpu().numpy(), b) <= 1e-8
+
+
+@pytest.mark.parametrize("raw", [False, True])
+def test_block_gnn_matches_oracle_and_solves(spai_lib, raw):
+    # 3 x 3 blocks (Sec. 3.2.2 with b = 3): node graph, 9-wide edge features
+    # and decoder output, G written block by block into A's scalar pattern
+    from oracle import pcg
+    spai = spai_lib
+    A, feat = W.elastic3d(5)
+    L = 2 if raw else 4
+    blob = W.gnn_random_weights(4, L, msg_raw_edge=raw, b=3)
+    dA = spai.CSRMatrix.from_numpy(A.n, A.rowptr, A.colidx, A.val)
+    P = spai.build_pattern(dA, spai.PATTERN_FULL)
+    M = spai.gnn_precond(dA, P, torch.tensor(feat, device="cuda"), torch.tensor(blob, device="cuda"), d_node=4,
+                         n_layers=L, msg_edge=spai.MSG_RAW if raw else spai.MSG_LATENT, g_dtype=spai.F32, eps=0.3,
+                         block=3)
+    g, gt = (t.cpu().numpy() for t in M.export(spai.F64))
+    ref = gnn.gnn_forward_blocks(A.n, A.rowptr, A.colidx, A.val, feat, blob, 3, n_layers=L, msg_raw_edge=raw)
+    assert np.abs(g - ref).max() <= TOL * np.abs(ref).max()
+    perm = P.export()["perm"].cpu().numpy()
+    assert np.array_equal(gt[perm], g)
+    b = W.rhs_uniform(A.n, 17)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = spai.pcg_solve(dA, M, torch.tensor(b, device="cuda"), x, precision=spai.PREC_MIXED, rtol=1e-8,
+                       max_iter=100000)
+    assert r["status"] == 0
+    assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x.cpu().numpy(), b) <= 1e-8
+
+
+def test_block_gnn_rejects_non_block_matrix(spai_lib):
+    spai = spai_lib
+    A = W.poisson2d(6)                    # 36 rows, but not dense 3 x 3 blocks
+    dA = spai.CSRMatrix.from_numpy(A.n, A.rowptr, A.colidx, A.val)
+    P = spai.build_pattern(dA, spai.PATTERN_FULL)
+    blob = W.gnn_random_weights(1, 1, b=3)
+    with pytest.raises(spai.SpaiError) as ei:
+        spai.gnn_precond(dA, P, torch.zeros(12, 1, device="cuda"), torch.tensor(blob, device="cuda"), d_node=1,
+                         n_layers=1, g_dtype=spai.F32, eps=0.3, block=3)
+    assert ei.value.code == spai.spai.ERR_BAD_CSR
