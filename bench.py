@@ -651,7 +651,8 @@ def run_serve(args):
                 A_h = W.graph_laplacian(nn, 8 * nn, seed=W.BASE_SEED + 300 + j)
                 feat, d_node, blob = W.row_average_feature(A_h), 1, blob1
             A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
-            P32, M32 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, spai.F32, args.eps)
+            gdt_srv = spai.BF16 if args.serve_gdtype == "bf16" else spai.F32
+            P32, M32 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, gdt_srv, args.eps)
             P64, M64 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, spai.F64, args.eps)
             S = spai.system_create(A)
             pool.append({"gen": gen, "n": A_h.n, "nnz": A_h.nnz, "A": A, "S": S, "M32": M32, "M64": M64,
@@ -735,6 +736,7 @@ def run_serve(args):
                         {"workload": f"{R} requests over 48 systems (Poisson 2D, diffusion 3D, graph Laplacian), "
                                      f"n log-uniform [{args.serve_n_lo}, {args.serve_n_hi}], Poisson arrivals",
                          "hbm_cap_gb": args.hbm_cap_gb, "max_slots": args.max_slots, "chunk_iters": args.chunk_iters,
+                         "served_g_dtype": args.serve_gdtype,
                          "eps": args.eps},
                         {"mu64_solves_per_s": mu64, "ratio_vs_f64_one_at_a_time": top["served"]["solves_per_s"] / mu64,
                          "rates": rates, "clocks": clk,
@@ -830,6 +832,7 @@ def main():
     ap.add_argument("--rates", default="0.5,1,2,4,8")
     ap.add_argument("--serve-n-lo", type=int, default=10_000)
     ap.add_argument("--serve-n-hi", type=int, default=262_144)
+    ap.add_argument("--serve-gdtype", default="f32", choices=["f32", "bf16"], help="G storage of the served form")
     ap.add_argument("--hbm-cap-gb", type=int, default=120)
     ap.add_argument("--max-slots", type=int, default=64)
     ap.add_argument("--chunk-iters", type=int, default=16)
