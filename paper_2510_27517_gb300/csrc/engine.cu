@@ -132,7 +132,6 @@ template <> struct Conv<float> {
 constexpr int kBlock = 256;   // threads per block
 constexpr int kNE = 8;        // staged entries per thread per group
 constexpr int kCap = kNE * kBlock;
-constexpr int kRMax = 1;      // rows per thread whose operands are loaded together
 constexpr int kChunk = 32;    // items per first-level reduction chunk
 constexpr int kStages32 = 3;  // TMA stage ring depth (float32 kernels)
 constexpr int kStages64 = 2;  // TMA stage ring depth (float64 kernels)
@@ -347,8 +346,7 @@ struct Pipe {
   int* gent;                  // kMaxK + 1 group first entries
   int* rel;                   // kStages release counters (warps done with the stage's group)
   unsigned char* wbuf;        // per-warp product buffers (kWarpE entries of 8 bytes each)
-  uint32_t issued, consumed;  // groups issued / consumed by this block (uniform)
-  uint32_t blocks_seen;       // 32-row blocks of all groups consumed so far (uniform)
+  uint32_t consumed;          // groups consumed by this block (uniform)
 };
 
 // Thread 0: bulk-copy the entries of group g (rows tiles[g]..tiles[g+1]) into
@@ -837,9 +835,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   P.grow = s_grow;
   P.gent = s_gent;
   P.rel = s_rel;
-  P.issued = 0;
   P.consumed = 0;
-  P.blocks_seen = 0;
   void* sbuf = smem_raw + (size_t)L::kStages * L::kStageBytes;
   P.wbuf = static_cast<unsigned char*>(sbuf);  // shared with the direct path's buffer (never used at once)
   if (threadIdx.x == 0) {
