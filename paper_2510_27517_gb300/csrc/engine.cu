@@ -133,7 +133,8 @@ constexpr int kBlock = 256;   // threads per block
 constexpr int kNE = 8;        // staged entries per thread per group
 constexpr int kCap = kNE * kBlock;
 constexpr int kChunk = 32;    // items per first-level reduction chunk
-constexpr int kStages32 = 3;  // TMA stage ring depth (float32 kernels)
+constexpr int kStages32 = 3;  // TMA stage ring depth of CSR groups (float32 kernels)
+constexpr int kStagesSell32 = 3;  // ring depth of SELL-32 groups (float32 kernels)
 constexpr int kStages64 = 2;  // TMA stage ring depth (float64 kernels)
 constexpr int kStages = 4;    // largest ring (shared-memory arrays)
 constexpr int kMaxK = 64;     // groups per work item at most
@@ -323,49 +324,72 @@ template <class VT> struct OpResid64 {   // r64 = b - A64 x64;  r = rin = (VT) r
 
 // ---- TMA-fed groups ----
 // Shared memory of one block: kStages stages of (column indices, values) for
-// one group each, the product buffer, the stage mbarriers and group headers.
+// one group each.  SELL-32 groups use every stage; CSR groups use one stage
+// fewer in float32 kernels and keep the per-warp product buffers in the last
+// one (float64 kernels: after the stages); the direct path's buffer overlays
+// stage 0 (it runs only while the ring is idle: every piped call waits for
+// all of the copies it issues).  Mbarriers and group headers are static.
 template <class MV> struct StageLayout {
   static constexpr int kStageE = kCap + 2 * kAlignE;  // entries per stage buffer
   static constexpr int kColBytes = kStageE * 4;
   static constexpr int kValBytes = kStageE * (int)sizeof(MV);
   static constexpr int kStageBytes = kColBytes + kValBytes;
-  static constexpr int kStages = sizeof(MV) == 4 ? kStages32 : kStages64;
+  static constexpr int kStages = sizeof(MV) == 4 ? kStagesSell32 : kStages64;  // stages in the region
+  static constexpr int kCsrStages = sizeof(MV) == 4 ? kStages32 : kStages64;
 };
 
 struct GroupHdr {
   int r, re, e0, e0a, e1, r_al, staged, pad;
 };
 
+// The ring lives at fixed shared-memory addresses (no pointers held in
+// registers): the stage region is the block's dynamic shared memory.
+extern __shared__ __align__(128) unsigned char eng_smem[];
+__shared__ uint64_t eng_bar[kStages];       // stage mbarriers
+__shared__ GroupHdr eng_hdr[kStages];       // stage group headers
+__shared__ int eng_grow[kMaxK + 1];         // group row (or slice) starts of the current item
+__shared__ int eng_gent[kMaxK + 1];         // group first entries
+__shared__ int eng_rel[kStages];            // warps done with the stage's group
+
+// Per-thread ring state (uniform over the block).
 struct Pipe {
-  unsigned char* stage_base;  // kStages * stage bytes
-  int stage_bytes;
-  int col_bytes;
-  uint64_t* bar;              // kStages mbarriers
-  GroupHdr* hdr;              // kStages headers
-  int* grow;                  // kMaxK + 1 group row starts of the current item
-  int* gent;                  // kMaxK + 1 group first entries
-  int* rel;                   // kStages release counters (warps done with the stage's group)
-  unsigned char* wbuf;        // per-warp product buffers (kWarpE entries of 8 bytes each)
-  uint32_t consumed;          // groups consumed by this block (uniform)
+  uint32_t par;  // parity of the next phase of each stage mbarrier
+  bool ok;       // false once a stage wait of this thread timed out
 };
+
+// Waits for stage st; false (and the error flag set) if it did not arrive in
+// time or an earlier wait of this warp timed out, so that a stage that may
+// hold stale column indices is never gathered from.
+__device__ __forceinline__ bool stage_wait(Pipe& P, int st, uint64_t limit_ns, int* err) {
+  if (!mbar_wait_bounded(eng_bar + st, (P.par >> st) & 1u, limit_ns)) {
+    atomicExch(err, SPAI_ERR_TIMEOUT);
+    P.ok = false;
+  }
+  P.par ^= 1u << st;
+  return __all_sync(0xffffffffu, P.ok);
+}
+
+template <class AT> __device__ __forceinline__ unsigned char* stage_ptr(int st) {
+  return eng_smem + (size_t)st * StageLayout<AT>::kStageBytes;
+}
 
 // Thread 0: bulk-copy the entries of group g (rows tiles[g]..tiles[g+1]) into
 // the next stage.  Copies start at a multiple of kAlignE entries (16-byte
 // aligned for every value type) and the arrays are padded past nnz.
-template <class MV>
-__device__ __forceinline__ void issue_group(Pipe& P, const int32_t* ci, const MV* val, int k, int st) {
-  const int r = P.grow[k], re = P.grow[k + 1];
-  const int e0 = P.gent[k], e1 = P.gent[k + 1];
+template <class AT, class MV>
+__device__ __forceinline__ void issue_group(const int32_t* ci, const MV* val, int k, int st) {
+  const int r = eng_grow[k], re = eng_grow[k + 1];
+  const int e0 = eng_gent[k], e1 = eng_gent[k + 1];
   const int e0a = e0 & ~(kAlignE - 1);
   int ne = ((e1 + kAlignE - 1) & ~(kAlignE - 1)) - e0a;
   if (ne < kAlignE) ne = kAlignE;
-  P.hdr[st] = GroupHdr{r, re, e0, e0a, e1, 0, 0, 0};
-  unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+  eng_hdr[st] = GroupHdr{r, re, e0, e0a, e1, 0, 0, 0};
+  unsigned char* base = stage_ptr<AT>(st);
   const unsigned cb = (unsigned)ne * 4u, vb = (unsigned)ne * (unsigned)sizeof(MV);
-  mbar_arrive_expect_tx(P.bar + st, cb + vb);
+  mbar_arrive_expect_tx(eng_bar + st, cb + vb);
   const uint64_t pol = l2_evict_first_policy();
-  tma_load_1d_hint(base, ci + e0a, cb, P.bar + st, pol);
-  tma_load_1d_hint(base + P.col_bytes, val + e0a, vb, P.bar + st, pol);
+  tma_load_1d_hint(base, ci + e0a, cb, eng_bar + st, pol);
+  tma_load_1d_hint(base + StageLayout<AT>::kColBytes, val + e0a, vb, eng_bar + st, pol);
 }
 
 // Processes groups [g0, g1) of one matrix through the stage ring.  Warps work
@@ -386,32 +410,30 @@ __device__ __forceinline__ void piped_groups(Pipe& P, const int32_t* __restrict_
   // bounds of every group of this item (row start, first entry), loaded once
   for (int i = threadIdx.x; i <= ng; i += blockDim.x) {
     const int r = __ldg(tiles + g0 + i);
-    P.grow[i] = r;
-    P.gent[i] = __ldg(rp + r);
+    eng_grow[i] = r;
+    eng_gent[i] = __ldg(rp + r);
   }
-  if (threadIdx.x < NS) P.rel[threadIdx.x] = 0;
+  if (threadIdx.x < NS) eng_rel[threadIdx.x] = 0;
+  fence_async_smem();  // earlier generic writes to the stages precede the bulk copies
   __syncthreads();
-  const uint32_t c0 = P.consumed;
   if (threadIdx.x == 0) {
     const int pre = ng < NS ? ng : NS;
-    for (int k = 0; k < pre; ++k) issue_group<MV>(P, ci, val, k, (int)((c0 + k) % NS));
+    for (int k = 0; k < pre; ++k) issue_group<AT, MV>(ci, val, k, k);
   }
-  AT* wb = reinterpret_cast<AT*>(P.wbuf) + warp * kWarpE;
+  AT* wb = reinterpret_cast<AT*>(stage_ptr<AT>(StageLayout<AT>::kCsrStages)) + warp * kWarpE;
   uint32_t blocks = 0;  // the deal of row blocks to warps restarts with every item
   for (int k = 0; k < ng; ++k) {
-    const uint32_t c = c0 + k;
-    const int st = (int)(c % NS);
-    const unsigned parity = (c / NS) & 1u;
-    if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
-    const GroupHdr h = P.hdr[st];
-    const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+    const int st = k % NS;
+    const bool go = stage_wait(P, st, limit_ns, err);
+    const GroupHdr h = eng_hdr[st];
+    const unsigned char* base = stage_ptr<AT>(st);
     const int32_t* cs = reinterpret_cast<const int32_t*>(base) - h.e0a;  // indexed by entry offset
-    const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) - h.e0a;
+    const MV* vs = reinterpret_cast<const MV*>(base + StageLayout<AT>::kColBytes) - h.e0a;
     const int nrows = h.re - h.r;
     const int nblk = (nrows + 31) >> 5;
     // first block of this group owned by this warp
     int j = (int)((uint32_t)(warp - (int)(blocks % NW) + NW) % NW);
-    for (; j < nblk; j += NW) {
+    for (; go && j < nblk; j += NW) {
       const int row = h.r + 32 * j + lane;
       const bool valid = row < h.re;
       int ea = 0, eb = 0;
@@ -457,15 +479,14 @@ __device__ __forceinline__ void piped_groups(Pipe& P, const int32_t* __restrict_
     // release the stage; the last warp refills it
     if (lane == 0) {
       __threadfence_block();
-      const int prev = atomicAdd(P.rel + st, 1);
+      const int prev = atomicAdd(eng_rel + st, 1);
       if (prev == NW - 1) {
-        P.rel[st] = 0;
-        if (k + NS < ng) issue_group<MV>(P, ci, val, k + NS, st);
+        eng_rel[st] = 0;
+        if (k + NS < ng) issue_group<AT, MV>(ci, val, k + NS, st);
       }
     }
     __syncwarp();
   }
-  P.consumed = c0 + ng;
   __syncthreads();
 }
 
@@ -487,35 +508,33 @@ __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict_
   constexpr int kB = 8;
   for (int i = threadIdx.x; i <= ng; i += blockDim.x) {
     const int sl = __ldg(tiles + g0 + i);
-    P.grow[i] = sl;
-    P.gent[i] = __ldg(sptr + sl);
+    eng_grow[i] = sl;
+    eng_gent[i] = __ldg(sptr + sl);
   }
-  if (threadIdx.x < NS) P.rel[threadIdx.x] = 0;
+  if (threadIdx.x < NS) eng_rel[threadIdx.x] = 0;
+  fence_async_smem();  // earlier generic writes to the stages precede the bulk copies
   __syncthreads();
-  const uint32_t c0 = P.consumed;
   if (threadIdx.x == 0) {
     const int pre = ng < NS ? ng : NS;
-    for (int k = 0; k < pre; ++k) issue_group<MV>(P, ci, val, k, (int)((c0 + k) % NS));
+    for (int k = 0; k < pre; ++k) issue_group<AT, MV>(ci, val, k, k);
   }
   uint32_t blocks = 0;
   for (int k = 0; k < ng; ++k) {
-    const uint32_t c = c0 + k;
-    const int st = (int)(c % NS);
-    const unsigned parity = (c / NS) & 1u;
+    const int st = k % NS;
     // slice offsets of the group, loaded before the wait (the group's slice
     // range is known from the item): lane l holds sptr[first + l] and
     // sptr[first + 32 + l]
-    const int gs0 = P.grow[k];
-    const int nsl = P.grow[k + 1] - gs0;
+    const int gs0 = eng_grow[k];
+    const int nsl = eng_grow[k + 1] - gs0;
     const int so0 = lane <= nsl ? __ldg(sptr + gs0 + lane) : 0;
     const int so1 = lane + 32 <= nsl ? __ldg(sptr + gs0 + 32 + lane) : 0;
-    if (!mbar_wait_bounded(P.bar + st, parity, limit_ns)) atomicExch(err, SPAI_ERR_TIMEOUT);
-    const GroupHdr h = P.hdr[st];
-    const unsigned char* base = P.stage_base + (size_t)st * P.stage_bytes;
+    const bool go = stage_wait(P, st, limit_ns, err);
+    const GroupHdr h = eng_hdr[st];
+    const unsigned char* base = stage_ptr<AT>(st);
     const int32_t* cs = reinterpret_cast<const int32_t*>(base) - h.e0a;
-    const MV* vs = reinterpret_cast<const MV*>(base + P.col_bytes) - h.e0a;
+    const MV* vs = reinterpret_cast<const MV*>(base + StageLayout<AT>::kColBytes) - h.e0a;
     int j = (int)((uint32_t)(warp - (int)(blocks % NW) + NW) % NW);
-    for (; j < nsl; j += NW) {
+    for (; go && j < nsl; j += NW) {
       const int sl = gs0 + j;
       int off, end;
       if (nsl <= kSlicesInReg) {
@@ -548,15 +567,14 @@ __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict_
     blocks += (uint32_t)nsl;
     if (lane == 0) {
       __threadfence_block();
-      const int prev = atomicAdd(P.rel + st, 1);
+      const int prev = atomicAdd(eng_rel + st, 1);
       if (prev == NW - 1) {
-        P.rel[st] = 0;
-        if (k + NS < ng) issue_group<MV>(P, ci, val, k + NS, st);
+        eng_rel[st] = 0;
+        if (k + NS < ng) issue_group<AT, MV>(ci, val, k + NS, st);
       }
     }
     __syncwarp();
   }
-  P.consumed = c0 + ng;
   __syncthreads();
 }
 
@@ -586,7 +604,7 @@ __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* t
                                            const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
                                            double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
                                            int* err, const int32_t* sptr = nullptr, int64_t n = 0) {
-  if (sptr) piped_slices<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, sptr, rp, ci, val, g0, g1, n,
+  if (sptr) piped_slices<(sizeof(AT) == 4 ? kStagesSell32 : kStages64), AT, MV>(P, tiles, sptr, rp, ci, val, g0, g1, n,
                                                                           op, p0, p1, limit_ns, err);
   else if (piped) piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0,
                                                                               p1, limit_ns, err);
@@ -816,30 +834,16 @@ __device__ __forceinline__ void load_state(const EngState* src, EngState* dst) {
 template <class VT, class GT, bool MIXED>
 __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   using MVmax = typename std::conditional<MIXED, float, double>::type;
-  using L = StageLayout<MVmax>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[64];
   __shared__ int sflag, s_last;
   __shared__ EngState s_st;
-  __shared__ uint64_t s_bar[kStages];
-  __shared__ GroupHdr s_hdr[kStages];
-  __shared__ int s_grow[kMaxK + 1], s_gent[kMaxK + 1];
-  __shared__ int s_rel[kStages];
 
   Pipe P;
-  P.stage_base = smem_raw;
-  P.stage_bytes = L::kStageBytes;
-  P.col_bytes = L::kColBytes;
-  P.bar = s_bar;
-  P.hdr = s_hdr;
-  P.grow = s_grow;
-  P.gent = s_gent;
-  P.rel = s_rel;
-  P.consumed = 0;
-  void* sbuf = smem_raw + (size_t)L::kStages * L::kStageBytes;
-  P.wbuf = static_cast<unsigned char*>(sbuf);  // shared with the direct path's buffer (never used at once)
+  P.par = 0;
+  P.ok = true;
+  void* sbuf = eng_smem;  // overlays stage 0: the ring is idle whenever the direct path runs
   if (threadIdx.x == 0) {
-    for (int i = 0; i < L::kStages; ++i) mbar_init(s_bar + i, 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(eng_bar + i, 1);  // every ring depth uses a prefix
     fence_mbar_init();
   }
   __syncthreads();
@@ -977,11 +981,21 @@ const void* select_kernel(bool mixed, int gtype) {
 
 }  // namespace
 
-size_t engine_smem_bytes(bool mixed) {
-  const int stage = mixed ? StageLayout<float>::kStageBytes * kStages32 : StageLayout<double>::kStageBytes * kStages64;
-  const size_t prod = (size_t)kCap * sizeof(double);                    // direct path
-  const size_t warp = (size_t)(kBlock / 32) * kWarpE * sizeof(double);  // pipelined path
-  return (size_t)stage + (prod > warp ? prod : warp);
+// Dynamic shared memory of a launch: the SELL-32 ring, the CSR ring with its
+// product buffers when a member streams CSR groups (csr_ring), and the
+// direct path's buffer over stage 0.  A launch without CSR groups leaves the
+// rest of the SM's shared-memory/L1 array to L1, where the vector gathers hit.
+size_t engine_smem_bytes(bool mixed, bool csr_ring = true) {
+  auto mx = [](size_t x, size_t y) { return x > y ? x : y; };
+  const size_t prod = (size_t)kCap * sizeof(double);
+  if (mixed) {
+    using L = StageLayout<float>;
+    const size_t csr = (size_t)L::kCsrStages * L::kStageBytes + (size_t)(kBlock / 32) * kWarpE * sizeof(float);
+    return mx(mx((size_t)L::kStages * L::kStageBytes, csr_ring ? csr : 0), prod);
+  }
+  using L = StageLayout<double>;
+  const size_t csr = (size_t)L::kCsrStages * L::kStageBytes + (size_t)(kBlock / 32) * kWarpE * sizeof(double);
+  return mx(mx((size_t)L::kStages * L::kStageBytes, csr_ring ? csr : 0), prod);
 }
 
 bool engine_groups_fit(int32_t max_row) { return max_row >= 1 && max_row <= kCap / 2; }
@@ -1065,9 +1079,10 @@ class EngineBatch {
     if (!kfn_)
       return set_error(SPAI_ERR_INVALID, mixed ? "mixed precision needs G stored as F32, BF16 or F16"
                                                : "float64 precision needs G stored as F64 or F32");
-    smem_ = engine_smem_bytes(mixed);
-    SPAI_CUDA(cudaFuncSetAttribute(kfn_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_));
-    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_, kfn_, kBlock, smem_));
+    smem_max_ = engine_smem_bytes(mixed);
+    smem_ = smem_max_;
+    SPAI_CUDA(cudaFuncSetAttribute(kfn_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
+    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_, kfn_, kBlock, smem_max_));
     if (per_sm_ < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
     grid_max_ = per_sm_ * num_sms();
     return SPAI_OK;
@@ -1084,6 +1099,7 @@ class EngineBatch {
     std::vector<EngSys> hs(nsys);
     int64_t items = 0, chunks = 0, nmax = 0;
     int live = 0;
+    bool csr_ring = false;  // a member streams CSR groups through the ring
     for (int i = 0; i < nsys; ++i) {
       const Member& mb = members[i];
       SystemData& A = *mb.S;
@@ -1150,6 +1166,7 @@ class EngineBatch {
       for (int mm = 0; mm < 3; ++mm) {
         e.fits[mm] = e.fmt[mm] ? 1 : fits;
         if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
+        if (!e.fmt[mm] && e.fits[mm]) csr_ring = true;
       }
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
@@ -1179,6 +1196,7 @@ class EngineBatch {
       if (mb.st.phase != PH_DONE) ++live;
     }
     if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
+    smem_ = engine_smem_bytes(mixed_, csr_ring);
     std::vector<int32_t> isys(items), itile(items);
     for (int i = 0; i < nsys; ++i)
       for (int v = 0; v < hs[i].nitems; ++v) {
@@ -1361,7 +1379,7 @@ class EngineBatch {
   cudaStream_t s_ = nullptr;
   spai_pcg_opts opts_;
   const void* kfn_ = nullptr;
-  size_t smem_ = 0;
+  size_t smem_ = 0, smem_max_ = 0;  // this launch's dynamic shared memory; the largest
   int per_sm_ = 0, grid_max_ = 0, grid_ = 0, nsys_ = 0, live_ = 0;
   int64_t max_iter_ = 0, slots_ = 0;
   DevMem tab_;
