@@ -321,8 +321,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch
 // atomics outweighs the serialised arrivals.)
 struct GridSync {
   unsigned count;  // blocks arrived
-  unsigned gen;
-  int exit_flag;   // decided by the last arriver, read by everyone after the barrier
+  unsigned gen;    // generation (counts in steps of 2); bit 0: the exit decided at the last barrier
+  int unused;
   int err;         // SPAI_ERR_TIMEOUT when a wait gave up
   int live;        // systems still running
   int slot;        // slots executed so far (parity of double-buffered state)
@@ -335,30 +335,34 @@ struct GridSync {
 // everyone's); the last arriver publishes the next generation with a release
 // store and the others acquire it, so writes made before the barrier by any
 // block are visible after it (the CTA barrier extends this to every thread).
+// The exit decision (no live system, or an error) travels in bit 0 of the
+// generation word, so a waiter needs no further load after its wait.
 __device__ __forceinline__ int grid_barrier(GridSync* g, unsigned nblocks, uint64_t limit_ns, int* sflag) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned my_gen = ld_relaxed_u32(&g->gen);
     const unsigned prev = atom_add_acq_rel_u32(&g->count, 1u);
+    unsigned ex;
     if (prev == nblocks - 1) {
       g->count = 0;
       const int live = *(volatile int*)&g->live;
       const int err = *(volatile int*)&g->err;
-      *(volatile int*)&g->exit_flag = (live <= 0 || err != 0) ? 1 : 0;
-      st_release_u32(&g->gen, my_gen + 1u);
+      ex = (live <= 0 || err != 0) ? 1u : 0u;
+      st_release_u32(&g->gen, ((my_gen | 1u) + 1u) | ex);
     } else {
       const uint64_t t0 = global_ns();
-      unsigned spins = 0;
-      while (ld_acquire_u32(&g->gen) == my_gen) {
+      unsigned spins = 0, v;
+      bool gave_up = false;
+      while ((v = ld_acquire_u32(&g->gen)) == my_gen) {
         if ((++spins & 1023u) == 0 && global_ns() - t0 > limit_ns) {
           atomicExch(&g->err, SPAI_ERR_TIMEOUT);
+          gave_up = true;
           break;
         }
       }
+      ex = gave_up ? 1u : (v & 1u);
     }
-    const int ef = *(volatile int*)&g->exit_flag;
-    const int er = *(volatile int*)&g->err;
-    *sflag = (ef || er) ? 1 : 0;
+    *sflag = (int)ex;
   }
   __syncthreads();
   return *sflag;
