@@ -599,19 +599,26 @@ __device__ __noinline__ void direct_rows(const int32_t* __restrict__ rp, const i
   spmv_rows<AT>(rp, ci, val, r0, r1, sbuf, red, op, p0, p1, blocks);
 }
 
-template <class AT, class MV, class Op>
+// CSR: the kernel streams CSR groups through the ring; kernels for launches
+// without such groups (every member SELL-32 or direct) leave that code out,
+// which keeps the SELL-32 loop free of its register pressure.
+template <class AT, bool CSR, class MV, class Op>
 __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* tiles, const int32_t* rp,
                                            const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
                                            double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
                                            int* err, const int32_t* sptr = nullptr, int64_t n = 0) {
   if (sptr) piped_slices<(sizeof(AT) == 4 ? kStagesSell32 : kStages64), AT, MV>(P, tiles, sptr, rp, ci, val, g0, g1, n,
                                                                           op, p0, p1, limit_ns, err);
-  else if (piped) piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0,
-                                                                              p1, limit_ns, err);
-  else direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op, p0, p1);
+  else if (CSR && piped) {
+    if constexpr (CSR)
+      piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0, p1,
+                                                                     limit_ns, err);
+  } else {
+    direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op, p0, p1);
+  }
 }
 
-template <class VT, class GT, bool MIXED>
+template <class VT, class GT, bool MIXED, bool CSR>
 __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P, void* sbuf,
                          double* red, double& p0, double& p1, uint64_t limit_ns, int* err) {
   const int rc = st.rc, dc = st.dc;
@@ -637,32 +644,32 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   switch (ph) {
     case PH_P1: {
       OpP1<VT> op{s, d_cur, d_nxt, q, beta, st.first != 0};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_P2: {
       OpP2<VT> op{r_cur, r_nxt, q, d_cur, xv, t, alpha};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_APPLY1: {
       OpApply1<VT> op{r_cur, t};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_APPLY2: {
       OpApply2<VT> op{t, r_cur, s, eps};
-      run_groups<VT>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       break;
     }
     case PH_RESID0:
     case PH_RESID: {
       if (!MIXED) {
         OpResid<VT> op{xv, S.b, r_cur};
-        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+        run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       } else {
         OpResidIn<VT> op{xv, rin, r_cur};
-        run_groups<VT>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+        run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
       }
       break;
     }
@@ -831,7 +838,7 @@ __device__ __forceinline__ void load_state(const EngState* src, EngState* dst) {
   for (int i = 0; i < (int)(sizeof(EngState) / 8); ++i) d[i] = __ldcg(s + i);
 }
 
-template <class VT, class GT, bool MIXED>
+template <class VT, class GT, bool MIXED, bool CSR>
 __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   using MVmax = typename std::conditional<MIXED, float, double>::type;
   __shared__ double red[64];
@@ -872,7 +879,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
       int g1 = g0 + K;
       if (g1 > S.ntiles[m]) g1 = S.ntiles[m];
       double p0 = 0.0, p1 = 0.0;
-      if (g0 < g1) run_item<VT, GT, MIXED>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err);
+      if (g0 < g1) run_item<VT, GT, MIXED, CSR>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err);
       block_sum2(p0, p1, red);
       double* pbase = a.partial + 2 * (size_t)S.item_base;
       double* cbase = a.cpartial + 2 * (size_t)S.chunk_base;
@@ -963,19 +970,20 @@ __global__ void engine_continue_kernel(GridSync* gs, int64_t slot_cap, cudaGraph
 }
 
 template <class VT, class GT, bool MIXED>
-const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED>);
+const void* kernel_ptr(bool csr) {
+  return csr ? reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, true>)
+             : reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, false>);
 }
 
-const void* select_kernel(bool mixed, int gtype) {
+const void* select_kernel(bool mixed, int gtype, bool csr) {
   if (!mixed) {
-    if (gtype == SPAI_F64) return kernel_ptr<double, double, false>();
-    if (gtype == SPAI_F32) return kernel_ptr<double, float, false>();
+    if (gtype == SPAI_F64) return kernel_ptr<double, double, false>(csr);
+    if (gtype == SPAI_F32) return kernel_ptr<double, float, false>(csr);
     return nullptr;
   }
-  if (gtype == SPAI_F32) return kernel_ptr<float, float, true>();
-  if (gtype == SPAI_BF16) return kernel_ptr<float, __nv_bfloat16, true>();
-  if (gtype == SPAI_F16) return kernel_ptr<float, __half, true>();
+  if (gtype == SPAI_F32) return kernel_ptr<float, float, true>(csr);
+  if (gtype == SPAI_BF16) return kernel_ptr<float, __nv_bfloat16, true>(csr);
+  if (gtype == SPAI_F16) return kernel_ptr<float, __half, true>(csr);
   return nullptr;
 }
 
@@ -1075,14 +1083,20 @@ class EngineBatch {
     mixed_ = mixed;
     s_ = s;
     opts_ = o;
-    kfn_ = select_kernel(mixed, gtype);
+    kfn_csr_ = select_kernel(mixed, gtype, true);
+    kfn_sell_ = select_kernel(mixed, gtype, false);
+    kfn_ = kfn_csr_;
     if (!kfn_)
       return set_error(SPAI_ERR_INVALID, mixed ? "mixed precision needs G stored as F32, BF16 or F16"
                                                : "float64 precision needs G stored as F64 or F32");
     smem_max_ = engine_smem_bytes(mixed);
     smem_ = smem_max_;
-    SPAI_CUDA(cudaFuncSetAttribute(kfn_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
-    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_, kfn_, kBlock, smem_max_));
+    int per_sell = 0;
+    SPAI_CUDA(cudaFuncSetAttribute(kfn_csr_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
+    SPAI_CUDA(cudaFuncSetAttribute(kfn_sell_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
+    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_, kfn_csr_, kBlock, smem_max_));
+    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sell, kfn_sell_, kBlock, smem_max_));
+    if (per_sell < per_sm_) per_sm_ = per_sell;  // one grid for both kernels
     if (per_sm_ < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
     grid_max_ = per_sm_ * num_sms();
     return SPAI_OK;
@@ -1197,6 +1211,7 @@ class EngineBatch {
     }
     if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
     smem_ = engine_smem_bytes(mixed_, csr_ring);
+    kfn_ = csr_ring ? kfn_csr_ : kfn_sell_;
     std::vector<int32_t> isys(items), itile(items);
     for (int i = 0; i < nsys; ++i)
       for (int v = 0; v < hs[i].nitems; ++v) {
@@ -1378,7 +1393,9 @@ class EngineBatch {
   bool mixed_ = false;
   cudaStream_t s_ = nullptr;
   spai_pcg_opts opts_;
-  const void* kfn_ = nullptr;
+  const void* kfn_ = nullptr;  // this launch's kernel: kfn_csr_ or kfn_sell_
+  const void* kfn_csr_ = nullptr;
+  const void* kfn_sell_ = nullptr;
   size_t smem_ = 0, smem_max_ = 0;  // this launch's dynamic shared memory; the largest
   int per_sm_ = 0, grid_max_ = 0, grid_ = 0, nsys_ = 0, live_ = 0;
   int64_t max_iter_ = 0, slots_ = 0;
@@ -1740,7 +1757,7 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
   const int64_t n = A->n;
 
   // kernel and grid
-  const void* kfn = select_kernel(false, SPAI_F64);
+  const void* kfn = select_kernel(false, SPAI_F64, true);
   const int block = kBlock;
   const size_t smem = engine_smem_bytes(false);
   SPAI_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
