@@ -579,24 +579,31 @@ __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict_
 }
 
 // Groups [g0, g1) without the stage ring (rows longer than a group, or the
-// float64 residual of mixed precision): direct loads.
+// float64 residual of mixed precision): direct loads.  Not inlined (rarely
+// run), so everything crosses the call by value: the item's partial sums
+// come back as the result instead of through references, which would keep
+// the caller's accumulators in local memory.
 template <class AT, class MV, class Op>
-__device__ __noinline__ void direct_groups(const int32_t* __restrict__ tiles, const int32_t* __restrict__ rp,
+__device__ __noinline__ double2 direct_groups(const int32_t* __restrict__ tiles, const int32_t* __restrict__ rp,
                                               const int32_t* __restrict__ ci, const MV* __restrict__ val, int g0,
-                                              int g1, AT* sbuf, double* red, const Op& op, double& p0, double& p1) {
+                                              int g1, AT* sbuf, double* red, const Op op) {
   uint32_t blocks = 0;
+  double p0 = 0.0, p1 = 0.0;
   for (int g = g0; g < g1; ++g)
     spmv_rows<AT>(rp, ci, val, __ldg(tiles + g), __ldg(tiles + g + 1), sbuf, red, op, p0, p1, blocks);
+  return make_double2(p0, p1);
 }
 
 // Rows [r0, r1) without the stage ring (float64 residual of mixed precision
 // over SELL-32 slices): direct loads.
 template <class AT, class MV, class Op>
-__device__ __noinline__ void direct_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                         const MV* __restrict__ val, int r0, int r1, AT* sbuf, double* red,
-                                         const Op& op, double& p0, double& p1) {
+__device__ __noinline__ double2 direct_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                            const MV* __restrict__ val, int r0, int r1, AT* sbuf, double* red,
+                                            const Op op) {
   uint32_t blocks = 0;
+  double p0 = 0.0, p1 = 0.0;
   spmv_rows<AT>(rp, ci, val, r0, r1, sbuf, red, op, p0, p1, blocks);
+  return make_double2(p0, p1);
 }
 
 // CSR: the kernel streams CSR groups through the ring; kernels for launches
@@ -614,7 +621,9 @@ __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* t
       piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0, p1,
                                                                      limit_ns, err);
   } else {
-    direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op, p0, p1);
+    const double2 q = direct_groups<AT, MV>(tiles, rp, ci, val, g0, g1, reinterpret_cast<AT*>(sbuf), red, op);
+    p0 += q.x;
+    p1 += q.y;
   }
 }
 
@@ -678,12 +687,17 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
         OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
         if (sp) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
           const int r0 = __ldg(tl + g0) * 32, r1 = (int)min((int64_t)__ldg(tl + g1) * 32, n);
-          if (r0 < r1)
-            direct_rows<double>(S.rp[MAT_A], S.a_ci64, S.a_v64, r0, r1, reinterpret_cast<double*>(sbuf), red, op,
-                                p0, p1);
+          if (r0 < r1) {
+            const double2 q =
+                direct_rows<double>(S.rp[MAT_A], S.a_ci64, S.a_v64, r0, r1, reinterpret_cast<double*>(sbuf), red, op);
+            p0 += q.x;
+            p1 += q.y;
+          }
         } else {
-          direct_groups<double>(tl, S.rp[MAT_A], S.a_ci64, S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red,
-                                op, p0, p1);
+          const double2 q =
+              direct_groups<double>(tl, S.rp[MAT_A], S.a_ci64, S.a_v64, g0, g1, reinterpret_cast<double*>(sbuf), red, op);
+          p0 += q.x;
+          p1 += q.y;
         }
       }
       break;
