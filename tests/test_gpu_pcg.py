@@ -192,6 +192,40 @@ def test_batched_equals_alone(spai_lib):
         assert torch.equal(xa, xb)
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_sell_and_csr_members_in_one_launch(spai_lib, mixed):
+    # a launch whose members all stream SELL-32 slices runs the kernel built
+    # without the CSR ring; a batch that also holds a CSR system runs the full
+    # kernel: each member's iteration is bit-identical either way
+    spai = spai_lib
+    gdt = spai.F32 if mixed else spai.F64
+    prec = spai.PREC_MIXED if mixed else spai.PREC_F64
+    A1, k1 = W.diffusion3d(14)
+    d1 = upload(spai, A1)
+    S1 = spai.system_create(d1)
+    assert S1.schedule()["sell"] == 1
+    P1 = spai.build_pattern(d1, spai.PATTERN_FULL)
+    M1 = spai.gnn_precond(d1, P1, torch.tensor(W.diffusion3d_node_features(k1), device="cuda"),
+                          torch.tensor(W.gnn_random_weights(4, 4), device="cuda"), d_node=4, g_dtype=gdt, eps=0.3)
+    A2 = W.aniso2d(40, 20.0, 0.7)
+    d2 = upload(spai, A2)
+    S2 = spai.system_create(d2)
+    S2.set_schedule(sell=0, staged=1)  # CSR row groups through the stage ring
+    M2, _ = fsai_precond(spai, A2, d2, gdt)
+    bs = [torch.tensor(W.rhs_uniform(A1.n, 41), device="cuda"), torch.tensor(W.rhs_uniform(A2.n, 42), device="cuda")]
+    alone = []
+    for S, M, b in ((S1, M1, bs[0]), (S2, M2, bs[1])):
+        x = torch.zeros(b.numel(), dtype=torch.float64, device="cuda")
+        r = spai.system_solve(S, M, b, x, precision=prec)
+        assert r["status"] == 0
+        alone.append((r, x))
+    xs = [torch.zeros_like(alone[0][1]), torch.zeros_like(alone[1][1])]
+    res = spai.pcg_solve_batched([S1, S2], [M1, M2], bs, xs, precision=prec)
+    for (ra, xa), rb, xb in zip(alone, res, xs):
+        assert rb["status"] == 0 and rb["iters"] == ra["iters"] and rb["outer_iters"] == ra["outer_iters"]
+        assert torch.equal(xa, xb)
+
+
 def test_mixed_reliable_updates_track_f64_iteration_count(spai_lib):
     # float32 iterations with float64 refinement of x and r reach the float64
     # rtol in about the float64 iteration count (the recurrence is not restarted)
