@@ -19,9 +19,11 @@ Contents (each function cites the passage of the paper it follows):
 * ``spectrum`` - kappa and Kaporin's condition number of M^-1 A (Sec. 4.5),
   dense, and the Ritz values of the CG / Lanczos tridiagonal matrix.
 * ``sai``      - the scale-invariant aligned-identity loss with probe vectors
-  (Sec. 3.3, Eqs. 7-8), forward value only.
+  (Sec. 3.3, Eqs. 7-8), forward value.
+* ``train``    - its gradient with respect to G and, by reverse-mode
+  differentiation of Eqs. 3-5, with respect to the GNN's weights (Sec. 3.3).
 
 All arithmetic is float64 (the paper fixes no precision).  The code is written
 for readability, not speed: plain numpy with no blocking or fusion.
 """
-from . import pattern, fsai, gnn, pcg, sai, spectrum  # noqa: F401
+from . import pattern, fsai, gnn, pcg, sai, spectrum, train  # noqa: F401
