@@ -178,6 +178,17 @@ int spai_ritz_kaporin(const double* alpha, const double* beta, int64_t k, double
  * ------------------------------------------------------------------------ */
 int spai_sai_loss(const spai_csr* A, const spai_precond* M, const double* w, int32_t k, double* loss, void* stream);
 
+/* Gradient of the SAI loss for training (Sec. 3.3): the loss of every probe
+ * as spai_sai_loss writes it, and in grad_g (device float64[nnz of G], the
+ * order of G's CSR in the pattern) the gradient of the mean loss over the k
+ * probes with respect to G's stored values:
+ *   dL/dG_ij = (2/k) sum_p (a_i (G^T w_p)_j + w_pi (G^T a)_j),
+ *   a = A (A M^-1 w_p / ||A|| - w_p) / ||A||  (A symmetric, as for every solve).
+ * G's values are read in their storage type and the arithmetic is float64.
+ * Same arguments and errors as spai_sai_loss. */
+int spai_sai_loss_grad(const spai_csr* A, const spai_precond* M, const double* w, int32_t k, double* loss,
+                       double* grad_g, void* stream);
+
 /* Self-test of the bounded device waits (no counterpart in the paper): runs
  * a kernel whose grid barrier and mbarrier can never complete, with a limit
  * of limit_us microseconds (1..1e6).  *detected = 1 when both waits gave up,

@@ -67,6 +67,45 @@ __global__ void loss_final_kernel(const double* __restrict__ part, int nb, int k
   }
 }
 
+// u = A v / ||A|| - w for k probes (the same arithmetic as the loss).
+__global__ void resid_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ val, const double* __restrict__ v,
+                             const double* __restrict__ w, const double* __restrict__ anorm, int64_t n, int k,
+                             double* __restrict__ u) {
+  const int lane = threadIdx.x & 31;
+  const double inv = 1.0 / anorm[0];
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+    if (lane >= k) continue;
+    double acc = 0.0;
+    for (int e = rp[row]; e < rp[row + 1]; ++e) acc = fma(val[e], v[(int64_t)ci[e] * k + lane], acc);
+    u[row * k + lane] = fma(acc, inv, -w[row * k + lane]);
+  }
+}
+
+// Gradient of the mean loss over the k probes with respect to every stored
+// G_ij (G's CSR order): (2 / k) sum_p (a_i y_j + w_i c_j) with a = A u / ||A||
+// and c = G^T a passed unscaled (as A u and G^T A u), y = G^T w.  One thread
+// per row, probes summed in order.
+__global__ void grad_g_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n, int k,
+                              const double* __restrict__ au, const double* __restrict__ y,
+                              const double* __restrict__ w, const double* __restrict__ cu,
+                              const double* __restrict__ anorm, double* __restrict__ grad) {
+  const double inv = 1.0 / anorm[0];
+  const double scale = 2.0 / (double)k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int64_t j = ci[e];
+      double acc = 0.0;
+      for (int p = 0; p < k; ++p) {
+        const double a = au[i * k + p] * inv, c = cu[j * k + p] * inv;
+        acc += a * y[j * k + p] + w[i * k + p] * c;
+      }
+      grad[e] = scale * acc;
+    }
+  }
+}
+
 template <class MV>
 int apply_minv(const PrecondData& M, const double* w, double* t, double* v, int64_t n, int k, cudaStream_t s) {
   const PatternData& P = *M.P;
@@ -115,6 +154,65 @@ extern "C" int spai_sai_loss(const spai_csr* A, const spai_precond* M, const dou
                                           nrm.as<double>(), n, k, rpb, part.as<double>());
   count_launch();
   loss_final_kernel<<<1, 32, 0, s>>>(part.as<double>(), nb, k, loss);
+  count_launch();
+  SPAI_CUDA(cudaGetLastError());
+  return SPAI_OK;
+}
+
+extern "C" int spai_sai_loss_grad(const spai_csr* A, const spai_precond* M, const double* w, int32_t k, double* loss,
+                                  double* grad_g, void* stream) {
+  if (!A || !M || !w || !loss || !grad_g) return set_error(SPAI_ERR_INVALID, "null argument");
+  if (k < 1 || k > kMaxProbes) return set_error(SPAI_ERR_INVALID, "k must be in 1..%d probes per call", kMaxProbes);
+  if (A->dtype != SPAI_F64) return set_error(SPAI_ERR_INVALID, "A values must be SPAI_F64");
+  const PrecondData& Md = *M->d;
+  const PatternData& P = *Md.P;
+  const int64_t n = A->n;
+  if (n <= 0 || P.n != n) return set_error(SPAI_ERR_SHAPE, "A and G sizes differ");
+  int rc;
+  if ((rc = spai_sai_loss(A, M, w, k, loss, stream))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevMem buf, nrm;
+  const size_t nk = (size_t)n * k;
+  if ((rc = buf.alloc(5 * nk * sizeof(double), s))) return rc;
+  if ((rc = nrm.alloc(sizeof(double), s))) return rc;
+  double* y = buf.as<double>();  // G^T w
+  double* v = y + nk;            // M^-1 w
+  double* u = v + nk;            // A v / ||A|| - w
+  double* au = u + nk;           // A u (A symmetric: A^T u)
+  double* cu = au + nk;          // G^T A u
+  if ((rc = matrix_abs_mean(static_cast<const double*>(A->val), A->nnz, nrm.as<double>(), s))) return rc;
+  switch (Md.gtype) {
+    case SPAI_F64: rc = apply_minv<double>(Md, w, y, v, n, k, s); break;
+    case SPAI_F32: rc = apply_minv<float>(Md, w, y, v, n, k, s); break;
+    case SPAI_BF16: rc = apply_minv<__nv_bfloat16>(Md, w, y, v, n, k, s); break;
+    case SPAI_F16: rc = apply_minv<__half>(Md, w, y, v, n, k, s); break;
+    default: return set_error(SPAI_ERR_INVALID, "unknown G storage type");
+  }
+  if (rc) return rc;
+  const int grid = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  const double* av = static_cast<const double*>(A->val);
+  resid_kernel<<<grid, 256, 0, s>>>(A->rowptr, A->colidx, av, v, w, nrm.as<double>(), n, k, u);
+  count_launch();
+  spmm_kernel<double><<<grid, 256, 0, s>>>(A->rowptr, A->colidx, av, u, au, n, k, nullptr, 0.0);
+  count_launch();
+  switch (Md.gtype) {
+    case SPAI_F64:
+      spmm_kernel<double><<<grid, 256, 0, s>>>(P.gt_rp(), P.gt_ci(), Md.gt_val.as<double>(), au, cu, n, k, nullptr, 0.0);
+      break;
+    case SPAI_F32:
+      spmm_kernel<float><<<grid, 256, 0, s>>>(P.gt_rp(), P.gt_ci(), Md.gt_val.as<float>(), au, cu, n, k, nullptr, 0.0);
+      break;
+    case SPAI_BF16:
+      spmm_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(P.gt_rp(), P.gt_ci(), Md.gt_val.as<__nv_bfloat16>(), au, cu, n, k,
+                                                      nullptr, 0.0);
+      break;
+    default:
+      spmm_kernel<__half><<<grid, 256, 0, s>>>(P.gt_rp(), P.gt_ci(), Md.gt_val.as<__half>(), au, cu, n, k, nullptr, 0.0);
+      break;
+  }
+  count_launch();
+  const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16);
+  grad_g_kernel<<<gg, 256, 0, s>>>(P.g_rp(), P.g_ci(), n, k, au, y, w, cu, nrm.as<double>(), grad_g);
   count_launch();
   SPAI_CUDA(cudaGetLastError());
   return SPAI_OK;

@@ -85,6 +85,8 @@ _SIGS = {
                                      C.POINTER(C.c_double)]),
     "spai_ritz_kaporin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "spai_sai_loss": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "spai_sai_loss_grad": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "spai_selftest_wait_timeout": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.c_void_p]),
     "spai_build_pattern": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_pattern_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -316,6 +318,18 @@ def sai_loss(A: CSRMatrix, M: Precond, w: torch.Tensor, stream=None) -> torch.Te
     out = torch.empty(w.shape[1], dtype=torch.float64, device=w.device)
     _check(lib().spai_sai_loss(C.byref(A._c()), M.h, _ptr(w), w.shape[1], _ptr(out), _stream(stream)))
     return out
+
+
+def sai_loss_grad(A: CSRMatrix, M: Precond, w: torch.Tensor, stream=None):
+    """Per-probe SAI loss and the gradient of its mean with respect to G's
+    stored values (float64, G's CSR order)."""
+    assert w.dtype == torch.float64 and w.is_cuda and w.dim() == 2 and w.shape[0] == A.n
+    w = w.contiguous()
+    loss = torch.empty(w.shape[1], dtype=torch.float64, device=w.device)
+    grad = torch.empty(M.pattern.info()[1], dtype=torch.float64, device=w.device)
+    _check(lib().spai_sai_loss_grad(C.byref(A._c()), M.h, _ptr(w), w.shape[1], _ptr(loss), _ptr(grad),
+                                    _stream(stream)))
+    return loss, grad
 
 
 def selftest_wait_timeout(limit_us=20000, stream=None) -> bool:
