@@ -74,17 +74,42 @@ def _mlp_bwd(p, cache, dy, grads):
     return dpre @ w1
 
 
-def gnn_forward_tape(n, rowptr, colidx, aval, node_feat, blob, n_layers=4, msg_raw_edge=False):
-    """G values on A's pattern (as ``gnn.gnn_forward``) and the tape the
-    reverse pass reads."""
-    node_feat = np.asarray(node_feat, dtype=np.float64).reshape(n, -1)
+def _block_positions(n, rowptr, browptr, b):
+    """Scalar CSR position of every entry of every b x b block, (nnzb, b, b),
+    in the layout ``gnn.block_graph`` reads (the inverse of
+    ``gnn.blocks_to_csr_values``)."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    pos = np.empty((int(browptr[-1]), b, b), dtype=np.int64)
+    for i in range(n // b):
+        for q in range(browptr[i + 1] - browptr[i]):
+            for r in range(b):
+                base = rowptr[b * i + r] + b * q
+                pos[browptr[i] + q, r] = base + np.arange(b)
+    return pos
+
+
+def gnn_forward_tape(n, rowptr, colidx, aval, node_feat, blob, n_layers=4, msg_raw_edge=False, b=1):
+    """G values on A's pattern (as ``gnn.gnn_forward``, or for b > 1 as
+    ``gnn.gnn_forward_blocks``: the GNN on the node graph of the b x b block
+    matrix) and the tape the reverse pass reads."""
+    aval = np.asarray(aval, dtype=np.float64)
+    nrm = gnn.matrix_norm(aval)
+    pos = None
+    if b == 1:
+        nodes, g_rowptr, g_colidx, eraw = n, rowptr, colidx, aval.reshape(-1, 1)
+    else:
+        nodes, g_rowptr, g_colidx, bval = gnn.block_graph(n, rowptr, colidx, aval, b)
+        eraw = bval.reshape(-1, b * b)
+        pos = _block_positions(n, rowptr, g_rowptr, b)
+    node_feat = np.asarray(node_feat, dtype=np.float64).reshape(nodes, -1)
     d_node = node_feat.shape[1]
-    params = gnn.unpack(blob, d_node, n_layers, msg_raw_edge, 1)
-    rows = np.repeat(np.arange(n), np.diff(np.asarray(rowptr, dtype=np.int64)))
-    cols = np.asarray(colidx, dtype=np.int64)
-    e = np.asarray(aval, dtype=np.float64).reshape(-1, 1) / gnn.matrix_norm(aval)
+    params = gnn.unpack(blob, d_node, n_layers, msg_raw_edge, b)
+    rows = np.repeat(np.arange(nodes), np.diff(np.asarray(g_rowptr, dtype=np.int64)))
+    cols = np.asarray(g_colidx, dtype=np.int64)
+    e = eraw / nrm
+    n = nodes
     tape = {"n": n, "rows": rows, "cols": cols, "params": params, "d_node": d_node, "n_layers": n_layers,
-            "msg_raw_edge": msg_raw_edge, "layers": []}
+            "msg_raw_edge": msg_raw_edge, "layers": [], "pos": pos, "b": b}
     x, tape["enc_n"] = _mlp_fwd(params[0], node_feat)
     h, tape["enc_e"] = _mlp_fwd(params[1], e)
     for t in range(n_layers):
@@ -99,7 +124,11 @@ def gnn_forward_tape(n, rowptr, colidx, aval, node_feat, blob, n_layers=4, msg_r
         h = h + dh
         tape["layers"].append((c_m, c_v, c_e))
     g, tape["dec"] = _mlp_fwd(params[-1], h)
-    return g[:, 0], tape
+    if pos is None:
+        return g[:, 0], tape
+    out = np.empty(int(np.asarray(rowptr)[-1]))
+    out[pos.reshape(-1)] = g.reshape(-1)
+    return out, tape
 
 
 def gnn_backward(tape, dg):
@@ -108,7 +137,12 @@ def gnn_backward(tape, dg):
     n, rows, cols, params = tape["n"], tape["rows"], tape["cols"], tape["params"]
     d = gnn.HIDDEN
     grads = [[np.zeros_like(a) for a in p] for p in params]
-    dh = _mlp_bwd(params[-1], tape["dec"], np.asarray(dg, dtype=np.float64).reshape(-1, 1), grads[-1])
+    dg = np.asarray(dg, dtype=np.float64)
+    if tape["pos"] is None:
+        dy = dg.reshape(-1, 1)
+    else:  # scalar CSR order -> one row of b^2 per block edge
+        dy = dg[tape["pos"].reshape(len(tape["pos"]), -1)]
+    dh = _mlp_bwd(params[-1], tape["dec"], dy, grads[-1])
     dx = np.zeros((n, d))
     for t in reversed(range(tape["n_layers"])):
         c_m, c_v, c_e = tape["layers"][t]
@@ -133,9 +167,9 @@ def gnn_backward(tape, dg):
     return np.concatenate(out)
 
 
-def loss_and_grad(n, rowptr, colidx, aval, node_feat, blob, eps, w, n_layers=4, msg_raw_edge=False):
-    """Mean SAI loss of the GNN's G (on A's full pattern) over the probes w,
-    and its gradient with respect to the weight blob."""
-    g, tape = gnn_forward_tape(n, rowptr, colidx, aval, node_feat, blob, n_layers, msg_raw_edge)
+def loss_and_grad(n, rowptr, colidx, aval, node_feat, blob, eps, w, n_layers=4, msg_raw_edge=False, b=1):
+    """Mean SAI loss of the GNN's G (on A's full pattern; b x b blocks for
+    b > 1) over the probes w, and its gradient with respect to the weight blob."""
+    g, tape = gnn_forward_tape(n, rowptr, colidx, aval, node_feat, blob, n_layers, msg_raw_edge, b)
     loss, dg = sai_loss_grad_g(n, rowptr, colidx, aval, rowptr, colidx, g, eps, w)
     return loss, gnn_backward(tape, dg)

@@ -176,3 +176,53 @@ def test_gradient_steps_lower_the_loss():
         assert cand < loss
         blob, loss, grad = blob - t * grad, cand, cgrad
     assert loss < 0.5 * first
+
+
+def _blocks():
+    A, feat = W.elastic3d(2)
+    blob = W.gnn_random_weights(4, 2, seed=21, b=3).astype(np.float64) * 1.5
+    return A, feat, blob
+
+
+def test_block_tape_forward_is_the_block_forward_oracle():
+    A, feat, blob = _blocks()
+    ref = gnn.gnn_forward_blocks(A.n, A.rowptr, A.colidx, A.val, feat, blob, 3, n_layers=2)
+    g, _ = train.gnn_forward_tape(A.n, A.rowptr, A.colidx, A.val, feat, blob, n_layers=2, b=3)
+    assert np.array_equal(g, ref)
+
+
+def test_block_gnn_backward_matches_central_differences():
+    # 3 x 3 blocks: the decoder writes 9 values per block edge, scattered to
+    # the scalar CSR; the reverse pass gathers them back
+    A, feat, blob = _blocks()
+    s = np.random.default_rng(12).standard_normal(A.nnz)
+    f = lambda b: float(s @ gnn.gnn_forward_blocks(A.n, A.rowptr, A.colidx, A.val, feat, b, 3, n_layers=2))  # noqa
+    _, tape = train.gnn_forward_tape(A.n, A.rowptr, A.colidx, A.val, feat, blob, n_layers=2, b=3)
+    grad = train.gnn_backward(tape, s)
+    assert grad.shape == blob.shape
+    # every decoder output weight and bias, and a sample of the rest
+    dec = gnn.HIDDEN * gnn.HIDDEN + gnn.HIDDEN + 9 * gnn.HIDDEN + 9
+    pick = np.concatenate([np.arange(blob.size - dec, blob.size),
+                           np.random.default_rng(13).choice(blob.size - dec, 120, replace=False)])
+    h = 1e-6
+    for k in pick:
+        bp, bm = blob.copy(), blob.copy()
+        bp[k] += h
+        bm[k] -= h
+        fd = (f(bp) - f(bm)) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * np.abs(grad).max(), k
+
+
+def test_block_full_chain_matches_central_differences():
+    A, feat, blob = _blocks()
+    w = np.random.default_rng(14).standard_normal((A.n, 2))
+    loss, grad = train.loss_and_grad(A.n, A.rowptr, A.colidx, A.val, feat, blob, 0.05, w, n_layers=2, b=3)
+    f = lambda b: train.loss_and_grad(A.n, A.rowptr, A.colidx, A.val, feat, b, 0.05, w, n_layers=2, b=3)[0]  # noqa
+    pick = np.random.default_rng(15).choice(blob.size, 40, replace=False)
+    h = 1e-6
+    for k in pick:
+        bp, bm = blob.copy(), blob.copy()
+        bp[k] += h
+        bm[k] -= h
+        fd = (f(bp) - f(bm)) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * np.abs(grad).max(), k
