@@ -1,0 +1,67 @@
+"""Host logic of bench.py (no GPU): the per-iteration byte model the roofline
+divides by, and the reading of the nvidia-smi clock record."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_algorithmic_bytes_per_iteration():
+    b = _bench()
+    n, nnz = 128 ** 3, 7 * 128 ** 3 - 6 * 128 ** 2  # 7-point stencil, Dirichlet boundary
+    assert nnz == 14_581_760
+    it, outer = b.algorithmic_bytes(n, nnz, nnz, 4, 4)
+    # three passes over 8-byte entries, row pointers, twelve float32 vector streams
+    assert it == 3 * nnz * 8 + 3 * (n + 1) * 4 + 12 * n * 4 == 475_791_372
+    # float64 outer step: A's values and indices, four float64 vectors
+    assert outer == nnz * 12 + 4 * n * 8
+    it16, _ = b.algorithmic_bytes(n, nnz, nnz, 4, 2)  # BF16 G
+    assert it - it16 == 2 * nnz * 2
+    it64, _ = b.algorithmic_bytes(n, nnz, nnz, 8, 8)
+    assert it64 == 3 * nnz * 12 + 3 * (n + 1) * 4 + 12 * n * 8
+
+
+def _sampler(lines):
+    b = _bench()
+    s = b.ClockSampler(0)
+    s.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0})()
+    s.lines = lines
+    return s
+
+
+def test_clock_record_median_under_load_and_reasons():
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active"] * 5
+    lines += ["0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active"] * 4
+    lines += ["0, 345, 2070, 120.0, 0x1, Not Active, Not Active, Not Active, Not Active"]  # idle sample
+    lines += ["garbled", "0, [N/A], 2070, 1, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    c = _sampler(lines).stop()
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["samples"] == 10
+
+
+@pytest.mark.parametrize("col,name", [(5, "hw_slowdown"), (6, "hw_thermal_slowdown"), (7, "sw_thermal_slowdown")])
+def test_clock_record_flags_throttling(col, name):
+    f = ["0", "1500", "2070", "1000", "0x8", "Not Active", "Not Active", "Not Active", "Not Active"]
+    f[col] = "Active"
+    c = _sampler([", ".join(f)]).stop()
+    assert c["reasons"] == [name]
+
+
+def test_clock_record_without_samples():
+    assert _sampler([]).stop()["reasons"] == ["no samples"]
+
+
+def test_replica_aggregate_is_whole_job_throughput():
+    b = _bench()
+    agg = b.aggregate([2000.0, 2500.0, 1800.0], steps=5, world=3)
+    assert agg["value"] == pytest.approx(3 * 5 / 2.5)
+    assert agg["ms_per_step"] == pytest.approx(500.0)
