@@ -249,6 +249,18 @@ int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const float* node
                      const spai_gnn_weights* W, int32_t g_dtype, double eps,
                      spai_precond** out, void* stream);
 
+/* Reverse pass of the GNN for training (Sec. 3.3 trains the GNN on the SAI
+ * loss): the gradient, with respect to every weight of the blob W describes,
+ * of sum_e dG[e] G[e], G the forward pass's output on A's full pattern P.
+ * dG: device float64[nnz of G] in P's CSR order (e.g. grad_g of
+ * spai_sai_loss_grad); dW: device float64[W->count] in the blob's layout.
+ * The forward pass is recomputed in float64 from the float32 weights and
+ * features and its activations kept (about (L + 1) 24 nnz + 8 x 72 nnz
+ * doubles of scratch); every sum is taken in a fixed order.  Scalar edges
+ * only (W->block 1).  Errors as spai_gnn_precond, SPAI_ERR_OOM. */
+int spai_gnn_grad(const spai_csr* A, const spai_pattern* P, const float* node_feat,
+                  const spai_gnn_weights* W, const double* dG, double* dW, void* stream);
+
 /* Preconditioner from caller-supplied values of G on P (device array of
  * nnz_g values of type val_dtype, F64 or F32, in P's CSR order), stored in
  * g_dtype.  Used for classical factors (FSAI, Jacobi, identity). */

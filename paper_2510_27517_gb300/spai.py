@@ -92,6 +92,8 @@ _SIGS = {
     "spai_pattern_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spai_pattern_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p]),
     "spai_pattern_destroy": (None, [C.c_void_p]),
+    "spai_gnn_grad": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.POINTER(_GNNW), C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
     "spai_gnn_precond": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.POINTER(_GNNW), C.c_int32,
                                    C.c_double, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_precond_from_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
@@ -274,6 +276,19 @@ def gnn_precond(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.T
     _check(lib().spai_gnn_precond(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), g_dtype, float(eps),
                                   C.byref(h), _stream(stream)))
     return Precond(h.value, P)
+
+
+def gnn_grad(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.Tensor, dG: torch.Tensor, d_node: int,
+             n_layers: int = 4, msg_edge=MSG_LATENT, stream=None) -> torch.Tensor:
+    """Gradient of sum(dG * G) with respect to the weight blob (float64)."""
+    assert node_feat.dtype == torch.float32 and node_feat.is_contiguous()
+    assert blob.dtype == torch.float32 and blob.is_contiguous()
+    assert dG.dtype == torch.float64 and dG.is_contiguous()
+    w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge, 1)
+    out = torch.empty(blob.numel(), dtype=torch.float64, device=blob.device)
+    _check(lib().spai_gnn_grad(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), _ptr(dG), _ptr(out),
+                               _stream(stream)))
+    return out
 
 
 def precond_from_values(P: Pattern, g_val: torch.Tensor, g_dtype=F64, eps=0.0, stream=None) -> Precond:

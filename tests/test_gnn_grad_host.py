@@ -1,0 +1,73 @@
+"""The GNN reverse pass of the CUDA library, run by a host executor of the
+same driver and element functions (tests/gnn_grad_host.cpp, built here with
+g++), against the oracle's reverse pass (itself pinned by central
+differences in test_oracle_train.py)."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import train
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+_LIB = None
+
+
+def host_lib():
+    global _LIB
+    if _LIB is None:
+        out = os.path.join(tempfile.mkdtemp(prefix="gnn_grad_host_"), "libgnn_grad_host.so")
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-ffp-contract=off",
+                               "-I", os.path.join(ROOT, "paper_2510_27517_gb300", "csrc"),
+                               os.path.join(ROOT, "tests", "gnn_grad_host.cpp"), "-o", out])
+        _LIB = ctypes.CDLL(out)
+        _LIB.gnn_grad_host.restype = ctypes.c_int
+    return _LIB
+
+
+def host_grad(A, v, blob, n_layers, raw, dg):
+    P = ctypes.c_void_p
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+    av = np.ascontiguousarray(A.val, dtype=np.float64)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    w = np.ascontiguousarray(blob, dtype=np.float64)
+    dg = np.ascontiguousarray(dg, dtype=np.float64)
+    out = np.zeros_like(w)
+    rc = host_lib().gnn_grad_host(ctypes.c_int64(A.n), P(rp.ctypes.data), P(ci.ctypes.data), P(av.ctypes.data),
+                                  P(vv.ctypes.data), ctypes.c_int(vv.shape[1]), P(w.ctypes.data),
+                                  ctypes.c_int(n_layers), ctypes.c_int(int(raw)), P(dg.ctypes.data),
+                                  P(out.ctypes.data))
+    assert rc == 0, rc
+    return out
+
+
+@pytest.mark.parametrize("raw", [False, True])
+@pytest.mark.parametrize("n_layers", [0, 1, 3])
+def test_host_executor_matches_oracle_reverse_pass(raw, n_layers):
+    A = W.random_spd_sparse(40, 0.12, 23)
+    v = np.random.default_rng(1).uniform(-1, 1, size=(A.n, 3))
+    blob = W.gnn_random_weights(3, n_layers, seed=31, msg_raw_edge=raw).astype(np.float64) * 1.5
+    dg = np.random.default_rng(2).standard_normal(A.nnz)
+    _, tape = train.gnn_forward_tape(A.n, A.rowptr, A.colidx, A.val, v, blob, n_layers, raw)
+    want = train.gnn_backward(tape, dg)
+    got = host_grad(A, v, blob, n_layers, raw, dg)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_host_executor_sai_chain_on_a_stencil():
+    # dL/dG of the SAI loss (oracle) pushed through the host executor equals
+    # the oracle's full gradient in the weights
+    A, k = W.diffusion3d(4)
+    v = W.diffusion3d_node_features(k)
+    blob = W.gnn_random_weights(4, 2, seed=7).astype(np.float64)
+    w = np.random.default_rng(9).standard_normal((A.n, 3))
+    g, tape = train.gnn_forward_tape(A.n, A.rowptr, A.colidx, A.val, v, blob, 2)
+    _, dg = train.sai_loss_grad_g(A.n, A.rowptr, A.colidx, A.val, A.rowptr, A.colidx, g, 0.1, w)
+    _, want = train.loss_and_grad(A.n, A.rowptr, A.colidx, A.val, v, blob, 0.1, w, n_layers=2)
+    got = host_grad(A, v, blob, 2, False, dg)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
