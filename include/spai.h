@@ -255,8 +255,8 @@ int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const float* node
  * dG: device float64[nnz of G] in P's CSR order (e.g. grad_g of
  * spai_sai_loss_grad); dW: device float64[W->count] in the blob's layout.
  * The forward pass is recomputed in float64 from the float32 weights and
- * features and its activations kept (about (L + 1) 24 nnz + 8 x 72 nnz
- * doubles of scratch); every sum is taken in a fixed order.  Scalar edges
+ * features and its activations kept ((24 (L + 1) + 265) nnz doubles of
+ * scratch); every sum is taken in a fixed order.  Scalar edges
  * only (W->block 1).  Errors as spai_gnn_precond, SPAI_ERR_OOM. */
 int spai_gnn_grad(const spai_csr* A, const spai_pattern* P, const float* node_feat,
                   const spai_gnn_weights* W, const double* dG, double* dW, void* stream);
