@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import train
+from oracle import gnn, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 _LIB = None
@@ -71,3 +71,43 @@ def test_host_executor_sai_chain_on_a_stencil():
     _, want = train.loss_and_grad(A.n, A.rowptr, A.colidx, A.val, v, blob, 0.1, w, n_layers=2)
     got = host_grad(A, v, blob, 2, False, dg)
     assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_host_executor_paper_configuration():
+    # the paper's configuration: 4 layers, d_node 4, latent messages, on a 3D
+    # diffusion stencil with its position + log-coefficient node features
+    A, k = W.diffusion3d(6)
+    v = W.diffusion3d_node_features(k)
+    blob = W.gnn_random_weights(4, 4).astype(np.float64)
+    dg = np.random.default_rng(4).standard_normal(A.nnz)
+    _, tape = train.gnn_forward_tape(A.n, A.rowptr, A.colidx, A.val, v, blob, 4)
+    want = train.gnn_backward(tape, dg)
+    got = host_grad(A, v, blob, 4, False, dg)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # every MLP receives a gradient (units whose ReLU is off everywhere get none)
+    o = 0
+    for fi, fo in gnn.layer_shapes(4, 4):
+        size = gnn.HIDDEN * fi + gnn.HIDDEN + fo * gnn.HIDDEN + fo
+        assert np.abs(got[o:o + size]).max() > 0
+        o += size
+
+
+def test_host_executor_rejects_unsymmetric_pattern():
+    A = W.random_spd_sparse(10, 0.3, 2)
+    keep = np.ones(A.nnz, dtype=bool)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    off = np.nonzero(A.colidx != rows)[0]
+    keep[off[0]] = False  # drop one off-diagonal entry: (i, j) stays, (j, i) goes
+    B = W.coo_to_csr(A.n, rows[keep], A.colidx[keep], A.val[keep])
+    rp = np.ascontiguousarray(B.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(B.colidx, dtype=np.int32)
+    av = np.ascontiguousarray(B.val)
+    v = np.zeros((B.n, 1))
+    w = W.gnn_random_weights(1, 1).astype(np.float64)
+    dg = np.zeros(B.nnz)
+    out = np.zeros_like(w)
+    P = ctypes.c_void_p
+    rc = host_lib().gnn_grad_host(ctypes.c_int64(B.n), P(rp.ctypes.data), P(ci.ctypes.data), P(av.ctypes.data),
+                                  P(v.ctypes.data), ctypes.c_int(1), P(w.ctypes.data), ctypes.c_int(1),
+                                  ctypes.c_int(0), P(dg.ctypes.data), P(out.ctypes.data))
+    assert rc == -1
