@@ -159,6 +159,9 @@ struct DevOps {
     SPAI_CUDA(cudaGetLastError());
     return SPAI_OK;
   }
+  void gather_dg(const double*, double*) {  // block edges: not taken by this executor yet
+    if (!rc) rc = SPAI_ERR_INVALID;
+  }
   void scale_edges(double* E) {
     scale_kernel<<<grid_for(nnz), kThreads, 0, s>>>(aval, anorm, nnz, E);
     count_launch();
@@ -258,5 +261,6 @@ extern "C" int spai_gnn_grad(const spai_csr* A, const spai_pattern* P, const flo
   ops.inv = inv;
   ops.aval = static_cast<const double*>(A->val);
   ops.anorm = nrm.as<double>();
-  return gg::gnn_grad_driver(ops, n, nnz, v64.as<double>(), W->d_node, w64.as<double>(), L, W->n_layers, raw, dG, dW);
+  return gg::gnn_grad_driver(ops, n, nnz, v64.as<double>(), W->d_node, w64.as<double>(), L, W->n_layers, raw, 1, dG,
+                             dW);
 }

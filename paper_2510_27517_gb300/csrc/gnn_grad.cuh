@@ -7,7 +7,9 @@
 // multiply-adds and every reduction sums in one fixed order, so given the
 // same ||A|| both executors give the same bits.
 //
-// The forward pass is recomputed in float64 with its activations kept:
+// The forward pass is recomputed in float64 with its activations kept (on
+// the node graph of the b x b block matrix for b > 1: e is then the block of
+// A / ||A|| flattened row-major and D writes a block of G per edge):
 //   x_0 = E_n(v),  h_0 = E_e(e),  e = A_ij / ||A||
 //   for t < L:  m_t = row sums of f_m(x_t[i], x_t[j], h_t or e)
 //               x_{t+1} = x_t + f_v(m_t)
@@ -109,7 +111,7 @@ struct Layout {
   int64_t off[2 + 3 * 8 + 2];
 };
 
-inline Layout make_layout(int d_node, int n_layers, bool raw) {
+inline Layout make_layout(int d_node, int n_layers, bool raw, int b2 = 1) {
   Layout L;
   auto add = [&](int fi, int fo) {
     L.fi[L.n_mlp] = fi;
@@ -117,13 +119,13 @@ inline Layout make_layout(int d_node, int n_layers, bool raw) {
     L.n_mlp++;
   };
   add(d_node, H);
-  add(1, H);
+  add(b2, H);
   for (int t = 0; t < n_layers; ++t) {
-    add(2 * H + (raw ? 1 : H), H);
+    add(2 * H + (raw ? b2 : H), H);
     add(H, H);
     add(3 * H, H);
   }
-  add(H, 1);
+  add(H, b2);
   L.off[0] = 0;
   for (int k = 0; k < L.n_mlp; ++k)
     L.off[k + 1] = L.off[k] + (int64_t)H * L.fi[k] + H + (int64_t)L.fo[k] * H + L.fo[k];
@@ -145,7 +147,8 @@ inline Mlp mlp_at(const double* w, const Layout& L, int k) {
 // The driver: one sequence of operations for both executors.  Ops provides
 // (arrays live in the executor's memory, float64, row-major):
 //   alloc(count) -> double*, zero(p, count), fail() / done() -> status
-//   scale_edges(E)                   E[e] = A_e / ||A||, ||A|| = mean |A_e| (Sec. 3.3)
+//   scale_edges(E)                   E[e] = A_e / ||A||, ||A|| = mean |A_e| (Sec. 3.3); b^2 per edge
+//   gather_dg(dG, DY)                DY[e][k] = dG at the scalar position of entry k of block edge e
 //   gather_edge(X, EI, de, Z, fi)    Z[e] = (X[row e], X[col e], EI[e][0:de]), fi = 2 H + de
 //   gather_rows(Xn, Z)               Z[e] = Xn[row e]                      (H wide)
 //   fwd(m, Z, N, Y, R)               Y[k] = mlp(Z[k]), plus R[k] when R is given
@@ -155,10 +158,14 @@ inline Mlp mlp_at(const double* w, const Layout& L, int k) {
 //   add_cols(In, ld, off, Out)       Out[e] += In[e][off:off+H]
 //   reduce(U, p, V, q, N, dst)       dst = the outer_partial sums over chunks of kChunk elements,
 //                                    chunk partials added in chunk order
+// n and nnz count the nodes and edges of the graph the GNN runs on (block
+// rows and blocks for b > 1); dG is in the scalar CSR order of G.
 template <class Ops>
 int gnn_grad_driver(Ops& ops, int64_t n, int64_t nnz, const double* v, int d_node, const double* w,
-                    const Layout& L, int n_layers, bool raw, const double* dG, double* dW) {
-  double* E = ops.alloc(nnz);  // e = A / ||A||
+                    const Layout& L, int n_layers, bool raw, int b2, const double* dG, double* dW) {
+  double* E = ops.alloc(nnz * b2);  // e = A / ||A||
+  double* DYD = b2 > 1 ? ops.alloc(nnz * b2) : nullptr;
+  if (!E || (b2 > 1 && !DYD)) return ops.fail();
   ops.scale_edges(E);
   // activations kept for the reverse pass
   double* X[9];
@@ -169,7 +176,7 @@ int gnn_grad_driver(Ops& ops, int64_t n, int64_t nnz, const double* v, int d_nod
     Hs[t] = ops.alloc(nnz * H);
     if (t < n_layers) M[t] = ops.alloc(n * H);
   }
-  const int fim = 2 * H + (raw ? 1 : H);
+  const int fim = 2 * H + (raw ? b2 : H);
   double* Z = ops.alloc(nnz * 3 * H);      // inputs of the largest edge MLP
   double* Y = ops.alloc(nnz * H);
   double* HID = ops.alloc(nnz * H);
@@ -188,7 +195,7 @@ int gnn_grad_driver(Ops& ops, int64_t n, int64_t nnz, const double* v, int d_nod
   ops.fwd(mlp_at(w, L, 1), E, nnz, Hs[0], nullptr);
   for (int t = 0; t < n_layers; ++t) {
     const Mlp fm = mlp_at(w, L, 2 + 3 * t), fv = mlp_at(w, L, 3 + 3 * t), fe = mlp_at(w, L, 4 + 3 * t);
-    ops.gather_edge(X[t], raw ? E : Hs[t], raw ? 1 : H, Z, fim);
+    ops.gather_edge(X[t], raw ? E : Hs[t], raw ? b2 : H, Z, fim);
     ops.fwd(fm, Z, nnz, Y, nullptr);
     ops.rowsum(Y, H, 0, M[t], true);
     ops.fwd(fv, M[t], n, X[t + 1], X[t]);
@@ -199,9 +206,14 @@ int gnn_grad_driver(Ops& ops, int64_t n, int64_t nnz, const double* v, int d_nod
   // ---- reverse ----
   const int kd = L.n_mlp - 1;
   const Mlp D = mlp_at(w, L, kd);
-  ops.bwd(D, Hs[n_layers], dG, nnz, HID, DPRE, DH);
+  const double* DG = dG;
+  if (b2 > 1) {
+    ops.gather_dg(dG, DYD);
+    DG = DYD;
+  }
+  ops.bwd(D, Hs[n_layers], DG, nnz, HID, DPRE, DH);
   ops.reduce(DPRE, H, Hs[n_layers], H, nnz, dW + L.off[kd]);
-  ops.reduce(dG, 1, HID, H, nnz, dW + L.off[kd] + (int64_t)H * H + H);
+  ops.reduce(DG, b2, HID, H, nnz, dW + L.off[kd] + (int64_t)H * H + H);
   ops.zero(DX, n * H);
   for (int t = n_layers - 1; t >= 0; --t) {
     const int km = 2 + 3 * t, kv = 3 + 3 * t, ke = 4 + 3 * t;
@@ -219,7 +231,7 @@ int gnn_grad_driver(Ops& ops, int64_t n, int64_t nnz, const double* v, int d_nod
     ops.reduce(DPRE, H, M[t], H, n, dW + L.off[kv]);
     ops.reduce(DX, H, HID, H, n, dW + L.off[kv] + (int64_t)H * H + H);
     // m_t = row sums of f_m(x_t[i], x_t[j], edge input)
-    ops.gather_edge(X[t], raw ? E : Hs[t], raw ? 1 : H, Z, fim);
+    ops.gather_edge(X[t], raw ? E : Hs[t], raw ? b2 : H, Z, fim);
     ops.gather_rows(DM, DYE);
     ops.bwd(fm, Z, DYE, nnz, HID, DPRE, DZ);
     ops.reduce(DPRE, H, Z, fim, nnz, dW + L.off[km]);
@@ -230,8 +242,8 @@ int gnn_grad_driver(Ops& ops, int64_t n, int64_t nnz, const double* v, int d_nod
   }
   // encoders
   ops.bwd(mlp_at(w, L, 1), E, DH, nnz, HID, DPRE, DZ);
-  ops.reduce(DPRE, H, E, 1, nnz, dW + L.off[1]);
-  ops.reduce(DH, H, HID, H, nnz, dW + L.off[1] + (int64_t)H * 1 + H);
+  ops.reduce(DPRE, H, E, b2, nnz, dW + L.off[1]);
+  ops.reduce(DH, H, HID, H, nnz, dW + L.off[1] + (int64_t)H * b2 + H);
   ops.bwd(mlp_at(w, L, 0), v, DX, n, HID, DPRE, DZ);
   ops.reduce(DPRE, H, v, d_node, n, dW + L.off[0]);
   ops.reduce(DX, H, HID, H, n, dW + L.off[0] + (int64_t)H * d_node + H);

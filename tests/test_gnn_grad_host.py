@@ -29,7 +29,7 @@ def host_lib():
     return _LIB
 
 
-def host_grad(A, v, blob, n_layers, raw, dg):
+def host_grad(A, v, blob, n_layers, raw, dg, b=1):
     P = ctypes.c_void_p
     rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
@@ -40,8 +40,8 @@ def host_grad(A, v, blob, n_layers, raw, dg):
     out = np.zeros_like(w)
     rc = host_lib().gnn_grad_host(ctypes.c_int64(A.n), P(rp.ctypes.data), P(ci.ctypes.data), P(av.ctypes.data),
                                   P(vv.ctypes.data), ctypes.c_int(vv.shape[1]), P(w.ctypes.data),
-                                  ctypes.c_int(n_layers), ctypes.c_int(int(raw)), P(dg.ctypes.data),
-                                  P(out.ctypes.data))
+                                  ctypes.c_int(n_layers), ctypes.c_int(int(raw)), ctypes.c_int(b),
+                                  P(dg.ctypes.data), P(out.ctypes.data))
     assert rc == 0, rc
     return out
 
@@ -109,5 +109,18 @@ def test_host_executor_rejects_unsymmetric_pattern():
     P = ctypes.c_void_p
     rc = host_lib().gnn_grad_host(ctypes.c_int64(B.n), P(rp.ctypes.data), P(ci.ctypes.data), P(av.ctypes.data),
                                   P(v.ctypes.data), ctypes.c_int(1), P(w.ctypes.data), ctypes.c_int(1),
-                                  ctypes.c_int(0), P(dg.ctypes.data), P(out.ctypes.data))
+                                  ctypes.c_int(0), ctypes.c_int(1), P(dg.ctypes.data), P(out.ctypes.data))
     assert rc == -1
+
+
+@pytest.mark.parametrize("raw", [False, True])
+def test_host_executor_block_gnn(raw):
+    # 3 x 3 blocks: the GNN on the node graph, 9-wide edge features and
+    # decoder output, the gradient gathered from the scalar CSR order
+    A, feat = W.elastic3d(3)
+    blob = W.gnn_random_weights(4, 2, seed=41, msg_raw_edge=raw, b=3).astype(np.float64) * 1.5
+    dg = np.random.default_rng(6).standard_normal(A.nnz)
+    _, tape = train.gnn_forward_tape(A.n, A.rowptr, A.colidx, A.val, feat, blob, 2, raw, b=3)
+    want = train.gnn_backward(tape, dg)
+    got = host_grad(A, feat, blob, 2, raw, dg, b=3)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
