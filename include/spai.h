@@ -256,8 +256,9 @@ int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const float* node
  * spai_sai_loss_grad); dW: device float64[W->count] in the blob's layout.
  * The forward pass is recomputed in float64 from the float32 weights and
  * features and its activations kept ((24 (L + 1) + 265) nnz doubles of
- * scratch); every sum is taken in a fixed order.  Scalar edges
- * only (W->block 1).  Errors as spai_gnn_precond, SPAI_ERR_OOM. */
+ * scratch); every sum is taken in a fixed order.  W->block 3: the GNN on
+ * the node graph of A's dense 3 x 3 blocks, as spai_gnn_precond.  Errors as
+ * spai_gnn_precond, SPAI_ERR_OOM. */
 int spai_gnn_grad(const spai_csr* A, const spai_pattern* P, const float* node_feat,
                   const spai_gnn_weights* W, const double* dG, double* dW, void* stream);
 

@@ -112,6 +112,63 @@ __global__ void add_cols_kernel(const double* __restrict__ In, int ld, int off, 
   }
 }
 
+// Node graph of a scalar CSR made of dense b x b blocks (block row i: scalar
+// rows b i .. b i + b - 1, equal lengths, columns in aligned runs of b):
+// block rows start at srp[b i] / b^2; every block's column, its b^2 values
+// (row-major) and their scalar positions.  Sets *bad on any other layout.
+__global__ void block_graph64_kernel(const int32_t* __restrict__ srp, const int32_t* __restrict__ sci,
+                                     const double* __restrict__ aval, int64_t nb, int b, int32_t* __restrict__ brp,
+                                     int32_t* __restrict__ bci, double* __restrict__ eraw, int64_t* __restrict__ pos,
+                                     int* bad) {
+  const int b2 = b * b;
+  GG_LOOP(i, nb) {
+    const int64_t r0 = (int64_t)b * i;
+    const int len = srp[r0 + 1] - srp[r0];
+    bool ok = len % b == 0 && srp[r0] % b2 == 0;
+    for (int r = 1; ok && r < b; ++r) ok = srp[r0 + r + 1] - srp[r0 + r] == len;
+    if (!ok) {
+      atomicOr(bad, 1);
+      continue;
+    }
+    const int64_t k0 = srp[r0] / b2;
+    brp[i] = (int32_t)k0;
+    if (i == nb - 1) brp[nb] = (int32_t)(k0 + len / b);
+    for (int q = 0; q < len / b; ++q) {
+      const int c0 = sci[srp[r0] + b * q];
+      if (c0 % b) atomicOr(bad, 1);
+      bci[k0 + q] = c0 / b;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) {
+          const int64_t at = srp[r0 + r] + (int64_t)b * q + c;
+          if (sci[at] != c0 + c) atomicOr(bad, 1);
+          eraw[(k0 + q) * b2 + r * b + c] = aval[at];
+          pos[(k0 + q) * b2 + r * b + c] = at;
+        }
+    }
+  }
+}
+
+// inv[position of (j, i) in row j] = the entry (i, j), by binary search in
+// row j (columns ascending); sets *bad when the mirror entry is missing.
+__global__ void mirror_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const int32_t* __restrict__ rows, int64_t nnz, int32_t* __restrict__ inv, int* bad) {
+  GG_LOOP(e, nnz) {
+    const int32_t i = rows[e], j = ci[e];
+    int lo = rp[j], hi = rp[j + 1] - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ci[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    if (lo < rp[j + 1] && ci[lo] == i) inv[lo] = (int32_t)e;
+    else atomicOr(bad, 1);
+  }
+}
+
+__global__ void gather_dg_kernel(const double* __restrict__ dG, const int64_t* __restrict__ pos, int64_t count,
+                                 double* __restrict__ DY) {
+  GG_LOOP(k, count) DY[k] = dG[pos[k]];
+}
+
 // Block c: the first-level partial of chunk c for every entry.
 __global__ void reduce_partial_kernel(const double* __restrict__ U, int p, const double* __restrict__ V, int q,
                                       int64_t N, double* __restrict__ part) {
@@ -137,8 +194,10 @@ struct DevOps {
   const int32_t* ci = nullptr;
   const int32_t* rows = nullptr;
   const int32_t* inv = nullptr;
-  const double* aval = nullptr;
+  const double* aval = nullptr;     // raw edge features, nnz x b2
   const double* anorm = nullptr;
+  const int64_t* pos = nullptr;     // scalar position of every block entry (b2 > 1)
+  int b2 = 1;
   std::deque<DevMem> pool;
   int rc = SPAI_OK;
 
@@ -159,11 +218,12 @@ struct DevOps {
     SPAI_CUDA(cudaGetLastError());
     return SPAI_OK;
   }
-  void gather_dg(const double*, double*) {  // block edges: not taken by this executor yet
-    if (!rc) rc = SPAI_ERR_INVALID;
+  void gather_dg(const double* dG, double* DY) {
+    gather_dg_kernel<<<grid_for(nnz * b2), kThreads, 0, s>>>(dG, pos, nnz * b2, DY);
+    count_launch();
   }
   void scale_edges(double* E) {
-    scale_kernel<<<grid_for(nnz), kThreads, 0, s>>>(aval, anorm, nnz, E);
+    scale_kernel<<<grid_for(nnz * b2), kThreads, 0, s>>>(aval, anorm, nnz * b2, E);
     count_launch();
   }
   void gather_edge(const double* X, const double* EI, int de, double* Z, int fi) {
@@ -225,42 +285,85 @@ extern "C" int spai_gnn_grad(const spai_csr* A, const spai_pattern* P, const flo
   if (W->d_node < 1 || W->d_node > 16) return set_error(SPAI_ERR_SHAPE, "d_node must be in 1..16");
   if (W->n_layers < 0 || W->n_layers > 8) return set_error(SPAI_ERR_SHAPE, "n_layers must be in 0..8");
   if (W->msg_edge != SPAI_MSG_LATENT && W->msg_edge != SPAI_MSG_RAW) return set_error(SPAI_ERR_INVALID, "msg_edge");
-  if (W->block > 1) return set_error(SPAI_ERR_INVALID, "the reverse pass takes scalar (1 x 1) edges only");
+  const int bs = W->block <= 0 ? 1 : W->block;
+  if (bs != 1 && bs != 3) return set_error(SPAI_ERR_INVALID, "block size must be 1 or 3");
+  if (A->n % bs != 0) return set_error(SPAI_ERR_SHAPE, "n is not a multiple of the block size");
+  const int b2 = bs * bs;
   const bool raw = W->msg_edge == SPAI_MSG_RAW;
-  const gg::Layout L = gg::make_layout(W->d_node, W->n_layers, raw);
+  const gg::Layout L = gg::make_layout(W->d_node, W->n_layers, raw, b2);
   if (W->count != L.off[L.n_mlp])
     return set_error(SPAI_ERR_SHAPE, "weight blob has %lld floats, layout needs %lld", (long long)W->count,
                      (long long)L.off[L.n_mlp]);
-  const int64_t n = A->n, nnz = A->nnz;
+  const int64_t ns = A->n, nnz_s = A->nnz;
+  const int64_t n = ns / bs;  // nodes of the graph the GNN runs on
   cudaStream_t s = (cudaStream_t)stream;
   int rc;
-  DevMem w64, v64, idx, nrm;
+  DevMem w64, v64, nrm, flag, brp, bci, eraw, pos, idx;
   if ((rc = w64.alloc((size_t)W->count * sizeof(double), s))) return rc;
   if ((rc = v64.alloc((size_t)n * W->d_node * sizeof(double), s))) return rc;
-  if ((rc = idx.alloc((size_t)2 * nnz * sizeof(int32_t), s))) return rc;
   if ((rc = nrm.alloc(sizeof(double), s))) return rc;
+  if ((rc = flag.alloc(sizeof(int), s))) return rc;
   to_f64_kernel<<<grid_for(W->count), kThreads, 0, s>>>(W->blob, W->count, w64.as<double>());
   count_launch();
   to_f64_kernel<<<grid_for(n * W->d_node), kThreads, 0, s>>>(node_feat, n * W->d_node, v64.as<double>());
   count_launch();
+  if ((rc = matrix_abs_mean(static_cast<const double*>(A->val), nnz_s, nrm.as<double>(), s))) return rc;
+  SPAI_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+  const int32_t* grp = Pd.g_rp();
+  const int32_t* gci = Pd.g_ci();
+  const double* ev = static_cast<const double*>(A->val);
+  int64_t nnz = nnz_s;
+  if (bs > 1) {
+    // the node graph: at most nnz_s / b2 blocks
+    const int64_t cap = nnz_s / b2;
+    if ((rc = brp.alloc((size_t)(n + 1) * sizeof(int32_t), s))) return rc;
+    if ((rc = bci.alloc((size_t)(cap > 0 ? cap : 1) * sizeof(int32_t), s))) return rc;
+    if ((rc = eraw.alloc((size_t)(cap > 0 ? cap : 1) * b2 * sizeof(double), s))) return rc;
+    if ((rc = pos.alloc((size_t)(cap > 0 ? cap : 1) * b2 * sizeof(int64_t), s))) return rc;
+    SPAI_CUDA(cudaMemsetAsync(brp.p, 0, (size_t)(n + 1) * sizeof(int32_t), s));
+    block_graph64_kernel<<<grid_for(n), kThreads, 0, s>>>(Pd.g_rp(), Pd.g_ci(), ev, n, bs, brp.as<int32_t>(),
+                                                          bci.as<int32_t>(), eraw.as<double>(), pos.as<int64_t>(),
+                                                          flag.as<int>());
+    count_launch();
+    int bad = 0;
+    SPAI_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    if (bad) return set_error(SPAI_ERR_SHAPE, "A is not made of aligned dense %d x %d blocks", bs, bs);
+    nnz = cap;
+    grp = brp.as<int32_t>();
+    gci = bci.as<int32_t>();
+    ev = eraw.as<double>();
+  }
+  if ((rc = idx.alloc((size_t)2 * (nnz > 0 ? nnz : 1) * sizeof(int32_t), s))) return rc;
   int32_t* rows = idx.as<int32_t>();
   int32_t* inv = rows + nnz;
-  rows_kernel<<<grid_for(n), kThreads, 0, s>>>(Pd.g_rp(), n, rows);
+  rows_kernel<<<grid_for(n), kThreads, 0, s>>>(grp, n, rows);
   count_launch();
-  inv_kernel<<<grid_for(nnz), kThreads, 0, s>>>(Pd.perm.as<int32_t>(), nnz, inv);
+  if (bs == 1) {
+    inv_kernel<<<grid_for(nnz), kThreads, 0, s>>>(Pd.perm.as<int32_t>(), nnz, inv);
+  } else {
+    mirror_kernel<<<grid_for(nnz), kThreads, 0, s>>>(grp, gci, rows, nnz, inv, flag.as<int>());
+  }
   count_launch();
-  if ((rc = matrix_abs_mean(static_cast<const double*>(A->val), nnz, nrm.as<double>(), s))) return rc;
+  if (bs > 1) {
+    int bad = 0;
+    SPAI_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    if (bad) return set_error(SPAI_ERR_SHAPE, "the block pattern is not symmetric");
+  }
   SPAI_CUDA(cudaGetLastError());
   DevOps ops;
   ops.s = s;
   ops.n = n;
   ops.nnz = nnz;
-  ops.rp = Pd.g_rp();
-  ops.ci = Pd.g_ci();
+  ops.rp = grp;
+  ops.ci = gci;
   ops.rows = rows;
   ops.inv = inv;
-  ops.aval = static_cast<const double*>(A->val);
+  ops.aval = ev;
   ops.anorm = nrm.as<double>();
-  return gg::gnn_grad_driver(ops, n, nnz, v64.as<double>(), W->d_node, w64.as<double>(), L, W->n_layers, raw, 1, dG,
+  ops.b2 = b2;
+  ops.pos = bs > 1 ? pos.as<int64_t>() : nullptr;
+  return gg::gnn_grad_driver(ops, n, nnz, v64.as<double>(), W->d_node, w64.as<double>(), L, W->n_layers, raw, b2, dG,
                              dW);
 }

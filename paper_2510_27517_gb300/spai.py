@@ -279,12 +279,13 @@ def gnn_precond(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.T
 
 
 def gnn_grad(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.Tensor, dG: torch.Tensor, d_node: int,
-             n_layers: int = 4, msg_edge=MSG_LATENT, stream=None) -> torch.Tensor:
-    """Gradient of sum(dG * G) with respect to the weight blob (float64)."""
+             n_layers: int = 4, msg_edge=MSG_LATENT, block=1, stream=None) -> torch.Tensor:
+    """Gradient of sum(dG * G) with respect to the weight blob (float64);
+    block=3 as in gnn_precond."""
     assert node_feat.dtype == torch.float32 and node_feat.is_contiguous()
     assert blob.dtype == torch.float32 and blob.is_contiguous()
     assert dG.dtype == torch.float64 and dG.is_contiguous()
-    w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge, 1)
+    w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge, block)
     out = torch.empty(blob.numel(), dtype=torch.float64, device=blob.device)
     _check(lib().spai_gnn_grad(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), _ptr(dG), _ptr(out),
                                _stream(stream)))
