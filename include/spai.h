@@ -368,11 +368,15 @@ int spai_pcg_solve_host(const spai_csr* A, const spai_precond* M, const double* 
  * process exits; it limits n to 131072 rows and each matrix to 4194304
  * stored entries (larger inputs return SPAI_ERR_TOO_LARGE, and so does any
  * input whose working set exceeds the array).  The first call on a device
- * looks up the array's device address; make that first call before any
- * stream capture.  Every call shares the array and reuses it from the
- * previous call: calls that overlap on the GPU (other streams or threads)
- * race, so the caller must serialise them.  res->engine_ms is not measured
- * (0) since timing events are not created.
+ * looks up the array's device address and keeps it for the rest of the
+ * process; make that first call before any stream capture, and do not use
+ * this entry point after cudaDeviceReset (the kept address would be stale).
+ * Every call validates the CSRs and steps the solver with small
+ * device-to-host reads, so it synchronises `stream` before it returns.
+ * Every call shares the array and reuses it from the previous call: calls
+ * that overlap on the GPU (other streams or threads) race, so the caller
+ * must serialise them.  res->engine_ms is not measured (0) since timing
+ * events are not created.
  * ------------------------------------------------------------------------ */
 int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, const spai_csr* GT, double eps, const double* b,
                            double* x, const spai_pcg_opts* opts, spai_pcg_result* res, void* stream);

@@ -162,6 +162,15 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _check_vec(t, n, name, cuda=True):
+    """A contiguous float64 vector of at least n entries on the expected side
+    (the library reads and writes n entries through its raw pointer)."""
+    assert t.dtype == torch.float64, f"{name} must be float64"
+    assert t.is_cuda == cuda, f"{name} must be a {'device' if cuda else 'host'} tensor"
+    assert t.is_contiguous(), f"{name} must be contiguous"
+    assert t.numel() >= n, f"{name} has {t.numel()} entries, the system has {n} rows"
+
+
 # ---------------------------------------------------------------------------
 @dataclasses.dataclass
 class CSRMatrix:
@@ -271,6 +280,7 @@ def gnn_precond(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.T
     """block=3: A made of dense 3 x 3 blocks, node_feat one row per block row."""
     assert node_feat.dtype == torch.float32 and node_feat.is_contiguous()
     assert blob.dtype == torch.float32 and blob.is_contiguous()
+    assert node_feat.numel() == (A.n // max(1, block)) * d_node, "node_feat must hold (n / block) x d_node values"
     w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge, block)
     h = C.c_void_p()
     _check(lib().spai_gnn_precond(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), g_dtype, float(eps),
@@ -284,7 +294,10 @@ def gnn_grad(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.Tens
     block=3 as in gnn_precond."""
     assert node_feat.dtype == torch.float32 and node_feat.is_contiguous()
     assert blob.dtype == torch.float32 and blob.is_contiguous()
-    assert dG.dtype == torch.float64 and dG.is_contiguous()
+    assert dG.dtype == torch.float64 and dG.is_contiguous() and dG.is_cuda
+    nodes = A.n // max(1, block)
+    assert node_feat.numel() == nodes * d_node, "node_feat must hold (n / block) x d_node values"
+    assert dG.numel() == P.info()[1], "dG must hold one value per entry of G"
     w = _GNNW(blob.data_ptr(), blob.numel(), d_node, n_layers, msg_edge, block)
     out = torch.empty(blob.numel(), dtype=torch.float64, device=blob.device)
     _check(lib().spai_gnn_grad(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), _ptr(dG), _ptr(out),
@@ -390,7 +403,8 @@ def _solve_rc(rc):
 
 
 def pcg_solve(A: CSRMatrix, M: Precond, b: torch.Tensor, x: torch.Tensor, stream=None, **kw):
-    assert b.dtype == torch.float64 and x.dtype == torch.float64 and b.is_cuda and x.is_cuda
+    _check_vec(b, A.n, "b")
+    _check_vec(x, A.n, "x")
     o = make_opts(**kw)
     r = _Res()
     _solve_rc(lib().spai_pcg_solve(C.byref(A._c()), M.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))
@@ -398,6 +412,8 @@ def pcg_solve(A: CSRMatrix, M: Precond, b: torch.Tensor, x: torch.Tensor, stream
 
 
 def system_solve(S: System, M: Precond, b: torch.Tensor, x: torch.Tensor, stream=None, **kw):
+    _check_vec(b, S.A.n, "b")
+    _check_vec(x, S.A.n, "x")
     o = make_opts(**kw)
     r = _Res()
     _solve_rc(lib().spai_system_solve(S.h, M.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))
@@ -406,6 +422,10 @@ def system_solve(S: System, M: Precond, b: torch.Tensor, x: torch.Tensor, stream
 
 def pcg_solve_batched(systems, preconds, bs, xs, stream=None, **kw):
     n = len(systems)
+    assert len(preconds) == n and len(bs) == n and len(xs) == n
+    for S, b, x in zip(systems, bs, xs):
+        _check_vec(b, S.A.n, "b")
+        _check_vec(x, S.A.n, "x")
     arr = lambda vals: (C.c_void_p * n)(*vals)  # noqa: E731
     o = make_opts(**kw)
     res = (_Res * n)()
@@ -417,7 +437,8 @@ def pcg_solve_batched(systems, preconds, bs, xs, stream=None, **kw):
 
 def pcg_solve_host(A: CSRMatrix, M: Precond, b_host, x_host, stream=None, **kw):
     """b_host, x_host: contiguous float64 CPU tensors (pinned for speed)."""
-    assert b_host.dtype == torch.float64 and not b_host.is_cuda and x_host.dtype == torch.float64
+    _check_vec(b_host, A.n, "b_host", cuda=False)
+    _check_vec(x_host, A.n, "x_host", cuda=False)
     o = make_opts(**kw)
     r = _Res()
     _solve_rc(lib().spai_pcg_solve_host(C.byref(A._c()), M.h, C.c_void_p(b_host.data_ptr()),
@@ -430,7 +451,9 @@ def pcg_solve_noalloc(A: CSRMatrix, G: CSRMatrix, GT: CSRMatrix, eps: float, b: 
     """float64 PCG that allocates no device memory (spai_pcg_solve_noalloc):
     G and GT are device CSRs of G and its explicit transpose; all working
     memory comes from the library's static device scratch array."""
-    assert b.dtype == torch.float64 and x.dtype == torch.float64 and b.is_cuda and x.is_cuda
+    _check_vec(b, A.n, "b")
+    _check_vec(x, A.n, "x")
+    assert G.n == A.n and GT.n == A.n and G.nnz == GT.nnz
     o = make_opts(**kw)
     r = _Res()
     a_c, g_c, gt_c = A._c(), G._c(), GT._c()

@@ -360,3 +360,24 @@ def test_bounded_waits_time_out_and_context_survives(spai_lib):
     M, _ = fsai_precond(spai, A, dA)
     res, x, _ = gpu_solve(spai, dA, M, W.rhs_uniform(A.n, 3))
     assert res["status"] == 0
+
+
+def test_host_buffer_solve_poisson64(spai_lib):
+    # spai_pcg_solve_host: b and x in (pinned) host memory, the copies inside
+    # the call; the 64 x 64 Poisson FSAI solve against the oracle
+    spai = spai_lib
+    A = W.poisson2d(64)
+    b = W.rhs_uniform(A.n, W.BASE_SEED + 1)
+    dA = upload(spai, A)
+    M, (urp, uci, gv) = fsai_precond(spai, A, dA)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, urp, uci, gv, 0.0), rtol=1e-8)
+    for pinned in (True, False):
+        b_h = torch.tensor(b)
+        x_h = torch.zeros(A.n, dtype=torch.float64)
+        if pinned:
+            b_h, x_h = b_h.pin_memory(), x_h.pin_memory()
+        res = spai.pcg_solve_host(dA, M, b_h, x_h)
+        assert res["status"] == 0 and res["iters"] == ref.iters
+        x = x_h.numpy()
+        assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+        assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x, b) <= 1e-8
