@@ -764,11 +764,19 @@ def run_probe(args):
     M = spai.gnn_precond(A, P, torch.tensor(h["v"], device="cuda"), torch.tensor(h["blob"], device="cuda"), d_node=4,
                          n_layers=4, g_dtype=spai.F32, eps=args.eps)
     x = torch.zeros(A_h.n, dtype=torch.float64, device="cuda")
-    r = spai.pcg_solve(A, M, torch.tensor(h["b"], device="cuda"), x, precision=spai.PREC_MIXED, rtol=0.0,
-                       max_iter=args.probe_iters)
+    S = spai.system_create(A)
+    S.set_schedule(fuse=args.probe_fuse)
+    prec = spai.PREC_MIXED if args.precision == "mixed" else spai.PREC_F64
+    if prec == spai.PREC_F64:
+        M.close()
+        M = spai.gnn_precond(A, P, torch.tensor(h["v"], device="cuda"), torch.tensor(h["blob"], device="cuda"),
+                             d_node=4, n_layers=4, g_dtype=spai.F64, eps=args.eps)
+    r = spai.system_solve(S, M, torch.tensor(h["b"], device="cuda"), x, precision=prec, rtol=0.0,
+                          max_iter=args.probe_iters)
     torch.cuda.synchronize()
     print(json.dumps({"probe": True, "n": A_h.n, "nnz": A_h.nnz, "iters": r["iters"], "engine_ms": r["engine_ms"],
-                      "slots": r["slots"]}))
+                      "ms_per_iter": r["engine_ms"] / max(1, r["iters"]), "slots": r["slots"],
+                      "fuse": args.probe_fuse, "precision": args.precision}))
 
 
 # ---------------------------------------------------------------------------
@@ -838,6 +846,8 @@ def main():
     ap.add_argument("--chunk-iters", type=int, default=16)
     ap.add_argument("--probe", action="store_true", help="one short solve for profiler captures")
     ap.add_argument("--probe-iters", type=int, default=30)
+    ap.add_argument("--probe-fuse", type=int, default=1, choices=[0, 1],
+                    help="probe: G^T and G passes in one grid step (1) or one step each (0)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-k", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=6, help=argparse.SUPPRESS)

@@ -190,8 +190,9 @@ int spai_sai_loss_grad(const spai_csr* A, const spai_precond* M, const double* w
                        double* grad_g, void* stream);
 
 /* Self-test of the bounded device waits (no counterpart in the paper): runs
- * a kernel whose grid barrier and mbarrier can never complete, with a limit
- * of limit_us microseconds (1..1e6).  *detected = 1 when both waits gave up,
+ * a kernel whose grid barrier, mbarrier and item-flag wait (the ordering of
+ * a fused step's two passes) can never complete, with a limit of limit_us
+ * microseconds (1..1e6) each.  *detected = 1 when all three waits gave up,
  * flagged SPAI_ERR_TIMEOUT and returned (the context stays usable). */
 int spai_selftest_wait_timeout(int64_t limit_us, int32_t* detected, void* stream);
 
@@ -290,12 +291,18 @@ void spai_precond_destroy(spai_precond* M);
  *               padding adds at most 25%) are read in that layout, one row
  *               per lane; 0: CSR row groups.  The group size of the SELL
  *               layout scales with tile_nnz.
+ *   fuse        1: the G^T and G passes of an iteration run in one grid-wide
+ *               step, a G work item starting once the G^T items whose rows
+ *               it reaches have finished (per-item flags instead of a
+ *               grid-wide barrier); 0: one grid-wide step per pass.  The
+ *               arithmetic is the same either way.
  * Per-row sums are the same in every schedule (entries in stored order);
  * dot products are summed in a schedule-dependent fixed order.
  * The default is the heuristic schedule (sell 1).  `autotune` nonzero makes
  * the first solve of the system (spai_system_solve or spai_pcg_solve_batched)
  * time short runs of every candidate (tile_nnz T0, T0/2, T0/4; items_log2
- * -1, 0, 1; SELL, CSR staged, CSR direct) with that solve's preconditioner
+ * -1, 0, 1; SELL, CSR staged, CSR direct; the heuristic schedule also with
+ * fuse 0) with that solve's preconditioner
  * and precision and keep the fastest; it is then fixed, so a system's
  * results are the same alone and in any batch.
  * ------------------------------------------------------------------------ */
@@ -306,6 +313,7 @@ typedef struct {
   int32_t items_log2;  /* -4..4 */
   int32_t staged;      /* 0 or 1 */
   int32_t sell;        /* 1: SELL-32 layout for the matrices that have one, 0: CSR row groups */
+  int32_t fuse;        /* 1: G^T and G passes in one grid-wide step (default), 0: separate steps */
   int32_t tuned;       /* out: 1 once the autotuner ran or a schedule was set */
 } spai_schedule;
 

@@ -274,6 +274,7 @@ extern "C" int spai_system_schedule(const spai_system* S, spai_schedule* out) {
   out->items_log2 = S->d->items_log2;
   out->staged = S->d->staged;
   out->sell = S->d->sell;
+  out->fuse = S->d->fuse;
   out->tuned = S->d->tuned;
   return SPAI_OK;
 }
@@ -285,12 +286,14 @@ extern "C" int spai_system_set_schedule(spai_system* S, const spai_schedule* sch
   if (sch->tile_nnz < 0 || sch->tile_nnz > t0)
     return set_error(SPAI_ERR_INVALID, "tile_nnz must be in 1..%d (0: default)", (int)t0);
   if (sch->items_log2 < -4 || sch->items_log2 > 4) return set_error(SPAI_ERR_INVALID, "items_log2 must be in -4..4");
-  if ((sch->staged != 0 && sch->staged != 1) || (sch->sell != 0 && sch->sell != 1))
-    return set_error(SPAI_ERR_INVALID, "staged and sell must be 0 or 1");
+  if ((sch->staged != 0 && sch->staged != 1) || (sch->sell != 0 && sch->sell != 1) ||
+      (sch->fuse != 0 && sch->fuse != 1))
+    return set_error(SPAI_ERR_INVALID, "staged, sell and fuse must be 0 or 1");
   d.tile_nnz = sch->tile_nnz ? sch->tile_nnz : t0;
   d.items_log2 = sch->items_log2;
   d.staged = sch->staged;
   d.sell = sch->sell;
+  d.fuse = sch->fuse;
   d.tuned = 1;
   return SPAI_OK;
 }

@@ -45,7 +45,7 @@ namespace spai {
 namespace {
 
 enum Phase : int32_t {
-  PH_RESID0 = 0, PH_APPLY1, PH_APPLY2, PH_P1, PH_P2, PH_P2X, PH_RESID, PH_XUPD, PH_RESID64, PH_ZEROX, PH_DONE
+  PH_RESID0 = 0, PH_APPLY1, PH_APPLY2, PH_P1, PH_P2, PH_P2X, PH_RESID, PH_XUPD, PH_RESID64, PH_ZEROX, PH_P2F, PH_DONE
 };
 enum Mat : int { MAT_A = 0, MAT_GT = 1, MAT_G = 2 };
 
@@ -68,7 +68,8 @@ struct EngSys {
   int32_t nitems;           // work items of this system
   int32_t item_base;
   int32_t chunk_base;     // first chunk counter / chunk partial of this system
-  int32_t pad0;
+  int32_t fuse;           // 1: the G^T and G passes share one grid step (PH_P2F), ordered by item flags
+  const int32_t* dep;     // fuse: per item, the first and last G^T-pass items whose rows its G rows reach
   int64_t n;
   double eps;
   const double* b;
@@ -115,6 +116,7 @@ struct EngArgs {
   unsigned* cnt;          // per system: chunks completed in this slot
   unsigned* ccnt;         // per chunk: tiles completed in this slot
   GridSync* gs;
+  unsigned* flags;        // per item: the grid step (+1) in which its G^T pass of a fused step completed
   EngOpts o;
   int32_t max_slots;
   int32_t cap;  // staging capacity in entries
@@ -613,7 +615,7 @@ template <class AT, bool CSR, class MV, class Op>
 __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* tiles, const int32_t* rp,
                                            const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
                                            double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
-                                           int* err, const int32_t* sptr = nullptr, int64_t n = 0) {
+                                           int* err, const int32_t* sptr, int64_t n) {
   if (sptr) piped_slices<(sizeof(AT) == 4 ? kStagesSell32 : kStages64), AT, MV>(P, tiles, sptr, rp, ci, val, g0, g1, n,
                                                                           op, p0, p1, limit_ns, err);
   else if (CSR && piped) {
@@ -629,8 +631,8 @@ __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* t
 
 template <class VT, class GT, bool MIXED, bool CSR>
 __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P, void* sbuf,
-                         double* red, double& p0, double& p1, uint64_t limit_ns, int* err) {
-  const int rc = st.rc, dc = st.dc;
+                         double* red, double& p0, double& p1, uint64_t limit_ns, int* err, int rc) {
+  const int dc = st.dc;
   VT* r_cur = reinterpret_cast<VT*>(S.r[rc]);
   VT* r_nxt = reinterpret_cast<VT*>(S.r[rc ^ 1]);
   VT* d_cur = reinterpret_cast<VT*>(S.d[dc]);
@@ -805,7 +807,7 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
       if (!(dq > 0.0) || !isfinite(dq)) { finish(SPAI_ERR_BREAKDOWN); return; }
       st.alpha = st.delta / dq;
       if (S.lanczos && st.iter < S.lanczos_len) S.lanczos[2 * st.iter] = st.alpha;
-      st.phase = (o.period > 0 && (st.iter % o.period) == 0) ? PH_P2X : PH_P2;
+      st.phase = (o.period > 0 && (st.iter % o.period) == 0) ? PH_P2X : (S.fuse ? PH_P2F : PH_P2);
       return;
     }
     case PH_P2: {
@@ -875,79 +877,174 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
     const int par = (slot0 + slots) & 1;
     EngState* cur = par ? a.st1 : a.st0;
     EngState* nxt = par ? a.st0 : a.st1;
-    int cached = -1;
-    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-      const int sid = __ldg(a.item_sys + it);
-      const int v = __ldg(a.item_tile + it);
-      if (sid != cached) {
-        if (threadIdx.x == 0) load_state(cur + sid, &s_st);
-        __syncthreads();
-        cached = sid;
-      }
-      const int ph = s_st.phase;
-      if (ph == PH_DONE) continue;
-      const EngSys& S = a.sys[sid];
-      const int m = phase_mat(ph);
-      const int K = S.kgroups[m];
-      const int g0 = v * K;
-      int g1 = g0 + K;
-      if (g1 > S.ntiles[m]) g1 = S.ntiles[m];
-      double p0 = 0.0, p1 = 0.0;
-      if (g0 < g1) run_item<VT, GT, MIXED, CSR>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err);
-      block_sum2(p0, p1, red);
-      double* pbase = a.partial + 2 * (size_t)S.item_base;
-      double* cbase = a.cpartial + 2 * (size_t)S.chunk_base;
-      const int nit = S.nitems;
-      const int nch = (nit + kChunk - 1) / kChunk;
-      const int ch = v / kChunk;
-      const int ch_size = min(kChunk, nit - ch * kChunk);
-      if (threadIdx.x == 0) {
-        pbase[2 * v] = p0;
-        pbase[2 * v + 1] = p1;
-        const unsigned prev = atom_add_acq_rel_u32(a.ccnt + S.chunk_base + ch, 1u);
-        s_last = (prev == (unsigned)(ch_size - 1)) ? 1 : 0;
-      }
-      __syncthreads();
-      if (s_last) {
-        // this block completed chunk `ch`: sum its item partials (one warp, fixed tree)
-        if (threadIdx.x < 32) {
-          const int tt = ch * kChunk + threadIdx.x;
-          double c0 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt) : 0.0;
-          double c1 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt + 1) : 0.0;
-          c0 = warp_sum(c0);
-          c1 = warp_sum(c1);
+    const unsigned epoch = (unsigned)(slot0 + slots) + 1u;
+    // Pass 0 runs every system's phase; pass 1 only the G pass of fused
+    // steps (PH_P2F), whose items wait for the flags pass 0 published.  Item
+    // v runs in block v % grid in both passes.
+    for (int pass = 0; pass < 2; ++pass) {
+      int cached = -1;
+      for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+        const int sid = __ldg(a.item_sys + it);
+        const int v = __ldg(a.item_tile + it);
+        if (sid != cached) {
+          if (threadIdx.x == 0) load_state(cur + sid, &s_st);
+          __syncthreads();
+          cached = sid;
+        }
+        const int ph0 = s_st.phase;
+        if (ph0 == PH_DONE) continue;
+        const bool fused = ph0 == PH_P2F;
+        if (pass == 1 && !fused) continue;
+        const int ph = fused ? (pass == 0 ? PH_P2 : PH_APPLY2) : ph0;
+        const EngSys& S = a.sys[sid];
+        const int m = phase_mat(ph);
+        const int K = S.kgroups[m];
+        const int g0 = v * K;
+        int g1 = g0 + K;
+        if (g1 > S.ntiles[m]) g1 = S.ntiles[m];
+        if (pass == 1)  // the G^T items whose rows this item's G rows reach are done
+          wait_items(ItemWait{a.flags + S.item_base, __ldg(S.dep + 2 * v), __ldg(S.dep + 2 * v + 1), epoch},
+                     a.limit_ns, &a.gs->err);
+        // the G pass of a fused step reads r' = r - alpha q, which the G^T pass wrote to r[rc ^ 1]
+        const int rc = pass == 1 ? (s_st.rc ^ 1) : s_st.rc;
+        double p0 = 0.0, p1 = 0.0;
+        if (g0 < g1) run_item<VT, GT, MIXED, CSR>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err,
+                                                  rc);
+        block_sum2(p0, p1, red);
+        double* pbase = a.partial + 2 * (size_t)S.item_base;
+        if (fused && pass == 0) {
+          // the G^T pass of a fused step: keep r'.r' for the step's reduction, publish the item
           if (threadIdx.x == 0) {
-            cbase[2 * ch] = c0;
-            cbase[2 * ch + 1] = c1;
-            a.ccnt[S.chunk_base + ch] = 0u;
-            const unsigned prev = atom_add_acq_rel_u32(a.cnt + sid, 1u);
-            s_last = (prev == (unsigned)(nch - 1)) ? 2 : 0;
+            pbase[2 * v + 1] = p0;
+            st_release_u32(a.flags + S.item_base + v, epoch);
+          }
+          continue;
+        }
+        double* cbase = a.cpartial + 2 * (size_t)S.chunk_base;
+        const int nit = S.nitems;
+        const int nch = (nit + kChunk - 1) / kChunk;
+        const int ch = v / kChunk;
+        const int ch_size = min(kChunk, nit - ch * kChunk);
+        if (threadIdx.x == 0) {
+          pbase[2 * v] = p0;
+          if (!fused) pbase[2 * v + 1] = p1;
+          const unsigned prev = atom_add_acq_rel_u32(a.ccnt + S.chunk_base + ch, 1u);
+          s_last = (prev == (unsigned)(ch_size - 1)) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+          // this block completed chunk `ch`: sum its item partials (one warp, fixed tree)
+          if (threadIdx.x < 32) {
+            const int tt = ch * kChunk + threadIdx.x;
+            double c0 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt) : 0.0;
+            double c1 = (threadIdx.x < ch_size) ? __ldcg(pbase + 2 * tt + 1) : 0.0;
+            c0 = warp_sum(c0);
+            c1 = warp_sum(c1);
+            if (threadIdx.x == 0) {
+              cbase[2 * ch] = c0;
+              cbase[2 * ch + 1] = c1;
+              a.ccnt[S.chunk_base + ch] = 0u;
+              const unsigned prev = atom_add_acq_rel_u32(a.cnt + sid, 1u);
+              s_last = (prev == (unsigned)(nch - 1)) ? 2 : 0;
+            }
+          }
+          __syncthreads();
+          if (s_last == 2) {
+            double q0 = 0.0, q1 = 0.0;
+            for (int tt = threadIdx.x; tt < nch; tt += blockDim.x) {
+              q0 += __ldcg(cbase + 2 * tt);
+              q1 += __ldcg(cbase + 2 * tt + 1);
+            }
+            block_sum2(q0, q1, red);
+            if (threadIdx.x == 0) {
+              EngState ns = s_st;
+              if (fused) {
+                // G^T pass (r'.r' in q1), then, unless it stopped the iteration, the G pass (r'.s in q0)
+                ns.phase = PH_P2;
+                transition<MIXED>(S, ns, q1, 0.0, a.o, a.gs);
+                if (ns.phase == PH_APPLY2) transition<MIXED>(S, ns, q0, 0.0, a.o, a.gs);
+              } else {
+                transition<MIXED>(S, ns, q0, q1, a.o, a.gs);
+              }
+              nxt[sid] = ns;
+              if (ns.phase == PH_DONE) cur[sid] = ns;
+              a.cnt[sid] = 0u;
+            }
           }
         }
         __syncthreads();
-        if (s_last == 2) {
-          double q0 = 0.0, q1 = 0.0;
-          for (int tt = threadIdx.x; tt < nch; tt += blockDim.x) {
-            q0 += __ldcg(cbase + 2 * tt);
-            q1 += __ldcg(cbase + 2 * tt + 1);
-          }
-          block_sum2(q0, q1, red);
-          if (threadIdx.x == 0) {
-            EngState ns = s_st;
-            transition<MIXED>(S, ns, q0, q1, a.o, a.gs);
-            nxt[sid] = ns;
-            if (ns.phase == PH_DONE) cur[sid] = ns;
-            a.cnt[sid] = 0u;
-          }
-        }
       }
-      __syncthreads();
     }
     ++slots;
     const int ex = grid_barrier(a.gs, gridDim.x, a.limit_ns, &sflag);
     if (ex || slots >= a.max_slots) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->slot = slot0 + slots;
+}
+
+// Item dependencies of a fused step: for every item, the range of producer
+// items (G^T pass) whose rows hold the columns that the item's rows of the
+// consumer matrix (G) reach.  One block per item: the column range of the
+// item's CSR entries, then the producer items by binary search over their
+// first rows.  Rows come in CSR row groups (sell 0) or 32-row slices (sell 1).
+__global__ void deps_kernel(const int32_t* __restrict__ rp_c, const int32_t* __restrict__ ci_c,
+                            const int32_t* __restrict__ tiles_c, int nt_c, int k_c, int sell_c,
+                            const int32_t* __restrict__ tiles_p, int nt_p, int k_p, int sell_p, int nitems,
+                            int64_t n, int32_t* __restrict__ dep) {
+  __shared__ int smin[kBlock / 32], smax[kBlock / 32];
+  auto row_of = [n](const int32_t* tiles, int g, int sell) -> int64_t {
+    const int64_t r = sell ? (int64_t)__ldg(tiles + g) * 32 : (int64_t)__ldg(tiles + g);
+    return r < n ? r : n;
+  };
+  for (int v = blockIdx.x; v < nitems; v += gridDim.x) {
+    const int g0 = v * k_c;
+    const int g1 = min(g0 + k_c, nt_c);
+    int lo = INT32_MAX, hi = -1;
+    if (g0 < g1) {
+      const int64_t r0 = row_of(tiles_c, g0, sell_c), r1 = row_of(tiles_c, g1, sell_c);
+      if (r0 < r1) {
+        const int64_t e0 = __ldg(rp_c + r0), e1 = __ldg(rp_c + r1);
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+          const int c = __ldg(ci_c + e);
+          lo = min(lo, c);
+          hi = max(hi, c);
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      smin[threadIdx.x >> 5] = lo;
+      smax[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kBlock / 32; ++w) {
+        lo = min(lo, smin[w]);
+        hi = max(hi, smax[w]);
+      }
+      int u_lo = 0, u_hi = -1;  // empty range: nothing to wait for
+      if (hi >= 0) {
+        // last producer item whose first row is <= c
+        auto item_of = [&](int c) {
+          int a = 0, b = nitems - 1;
+          while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            const int g = min(mid * k_p, nt_p);
+            if (row_of(tiles_p, g, sell_p) <= c) a = mid; else b = mid - 1;
+          }
+          return a;
+        };
+        u_lo = item_of(lo);
+        u_hi = item_of(hi);
+      }
+      dep[2 * v] = u_lo;
+      dep[2 * v + 1] = u_hi;
+    }
+    __syncthreads();
+  }
 }
 
 // ---- true residual ||b - A x|| / ||b|| (float64, deterministic) ----
@@ -1201,6 +1298,7 @@ class EngineBatch {
       const int kg = engine_scale_k(engine_items_k(ng, grid_max_), A.items_log2, ng);
       e.nitems = (ng + kg - 1) / kg;
       for (int mm = 0; mm < 3; ++mm) e.kgroups[mm] = (e.ntiles[mm] + e.nitems - 1) / e.nitems;
+      e.fuse = A.fuse ? 1 : 0;
       e.item_base = (int32_t)items;
       e.chunk_base = (int32_t)chunks;
       items += e.nitems;
@@ -1242,10 +1340,26 @@ class EngineBatch {
     const size_t off_sys = 0, off_st0 = al(sz_sys), off_st1 = off_st0 + al(sz_st), off_is = off_st1 + al(sz_st);
     const size_t off_it = off_is + al(sz_items), off_part = off_it + al(sz_items), off_cnt = off_part + al(sz_part);
     const size_t off_cpart = off_cnt + al(sz_cnt), off_ccnt = off_cpart + al(sz_cpart);
-    const size_t off_gs = off_ccnt + al(sz_ccnt), total = off_gs + al(sizeof(GridSync));
+    const size_t off_gs = off_ccnt + al(sz_ccnt), off_flags = off_gs + al(sizeof(GridSync));
+    const size_t off_dep = off_flags + al(sizeof(unsigned) * items);
+    const size_t total = off_dep + al(sizeof(int32_t) * 2 * items);
     if ((rc = tab_.alloc(total, s_))) return rc;
     char* tb = tab_.as<char>();
     SPAI_CUDA(cudaMemsetAsync(tb, 0, total, s_));
+    // item dependencies of fused steps (G pass on G^T-pass items)
+    for (int i = 0; i < nsys; ++i) {
+      EngSys& e = hs[i];
+      if (!e.fuse) continue;
+      int32_t* dep = reinterpret_cast<int32_t*>(tb + off_dep) + 2 * (size_t)e.item_base;
+      e.dep = dep;
+      const PrecondData& P = *members[i].M;
+      const int dgrid = e.nitems < 4 * num_sms() ? e.nitems : 4 * num_sms();
+      deps_kernel<<<dgrid, kBlock, 0, s_>>>(P.P->g_rp(), P.P->g_ci(), e.tiles[MAT_G], e.ntiles[MAT_G],
+                                            e.kgroups[MAT_G], e.fmt[MAT_G], e.tiles[MAT_GT], e.ntiles[MAT_GT],
+                                            e.kgroups[MAT_GT], e.fmt[MAT_GT], e.nitems, e.n, dep);
+      count_launch();
+      SPAI_CUDA(cudaGetLastError());
+    }
     SPAI_CUDA(cudaMemcpyAsync(tb + off_sys, hs.data(), sz_sys, cudaMemcpyHostToDevice, s_));
     SPAI_CUDA(cudaMemcpyAsync(tb + off_st0, hst.data(), sz_st, cudaMemcpyHostToDevice, s_));
     SPAI_CUDA(cudaMemcpyAsync(tb + off_st1, hst.data(), sz_st, cudaMemcpyHostToDevice, s_));
@@ -1272,6 +1386,7 @@ class EngineBatch {
     args_.cpartial = reinterpret_cast<double*>(tb + off_cpart);
     args_.ccnt = reinterpret_cast<unsigned*>(tb + off_ccnt);
     args_.gs = reinterpret_cast<GridSync*>(tb + off_gs);
+    args_.flags = reinterpret_cast<unsigned*>(tb + off_flags);
     int64_t max_iter = opts_.max_iter;
     if (max_iter <= 0) {
       max_iter = 10 * nmax;
@@ -1551,19 +1666,24 @@ __global__ void tune_rhs_kernel(double* b, double* x, int64_t n) {
 int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
   constexpr int kTuneIters = 12;
   const int32_t t0 = engine_tile_nnz(S->max_row);
-  struct Cand { int32_t tile, klog, staged, sell; };
+  struct Cand { int32_t tile, klog, staged, sell, fuse; };
   std::vector<Cand> cands;
   const bool has_sell = S->sell_a.nslices > 0 || M->P->sell.nslices > 0;
   for (int div : {1, 2, 4}) {
     const int32_t t = t0 / div;
     if (div > 1 && t < 256) continue;
     for (int kl : {0, -1, 1}) {
-      if (has_sell) cands.push_back(Cand{t, kl, 1, 1});
+      if (has_sell) cands.push_back(Cand{t, kl, 1, 1, 1});
       for (int st : {1, 0}) {
         if (st == 0 && !engine_groups_fit(S->max_row)) continue;  // direct loads either way
-        cands.push_back(Cand{t, kl, st, 0});
+        cands.push_back(Cand{t, kl, st, 0, 1});
       }
     }
+  }
+  {
+    Cand c = cands[0];  // the heuristic schedule with one grid step per pass
+    c.fuse = 0;
+    cands.push_back(c);
   }
   DevMem buf;
   int rc;
@@ -1583,6 +1703,7 @@ int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
     S->items_log2 = c.klog;
     S->staged = c.staged;
     S->sell = c.sell;
+    S->fuse = c.fuse;
     double t = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
       tune_rhs_kernel<<<256, 256, 0, s>>>(b, x, S->n);
@@ -1604,6 +1725,7 @@ int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
   S->items_log2 = best.klog;
   S->staged = best.staged;
   S->sell = best.sell;
+  S->fuse = best.fuse;
   S->tuned = 1;
   set_error(SPAI_OK, "no error");
   return SPAI_OK;

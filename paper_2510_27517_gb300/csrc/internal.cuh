@@ -113,6 +113,7 @@ struct SystemData {
   int32_t items_log2 = 0;    // groups per work item = heuristic count * 2^items_log2
   int32_t staged = 1;        // 1: groups staged by TMA bulk copies (when rows fit), 0: direct loads
   int32_t sell = 1;          // 1: SELL-32 layout for matrices that have one, 0: CSR row groups
+  int32_t fuse = 1;          // 1: G^T and G passes in one grid step ordered by item flags
   int32_t autotune = 0;      // pick the schedule by timing candidates on the first solve
   int32_t tuned = 0;
   TileSet tiles;
@@ -168,6 +169,7 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -366,6 +368,50 @@ __device__ __forceinline__ int grid_barrier(GridSync* g, unsigned nblocks, uint6
   }
   __syncthreads();
   return *sflag;
+}
+
+// ---- item flags: ordering of the two passes of a fused grid step ----
+// A G-pass item may start gathering t once every G^T-pass item whose rows it
+// reaches has published the current step's epoch.  Warp 0 polls the flags
+// with relaxed loads (an acquire per poll would invalidate L1 for the other
+// blocks of the SM), then one acquire fence makes the producers' writes
+// visible and the block barrier extends that to every thread.  Bounded: on
+// expiry the error flag is set and the step's results are dropped.
+struct ItemWait {
+  const unsigned* f;  // nullptr: no wait
+  int lo, hi;         // inclusive item range
+  unsigned epoch;
+};
+
+static __device__ __noinline__ void wait_items(const ItemWait W, uint64_t limit_ns, int* err) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    uint64_t t0 = 0;
+    unsigned spins = 0;
+    bool expired = false;
+    for (int u0 = W.lo; u0 <= W.hi && !expired; u0 += 32) {
+      const int u = u0 + lane;
+      bool ready = u > W.hi || (int)(ld_relaxed_u32(W.f + u) - W.epoch) >= 0;
+      while (!__all_sync(0xffffffffu, ready)) {
+        if (!ready) ready = (int)(ld_relaxed_u32(W.f + u) - W.epoch) >= 0;
+        if ((++spins & 255u) == 0) {
+          int ex = 0;
+          if (lane == 0) {
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > limit_ns) ex = 1;
+          }
+          if (__shfl_sync(0xffffffffu, ex, 0)) {
+            if (lane == 0) atomicExch(err, SPAI_ERR_TIMEOUT);
+            expired = true;
+            break;
+          }
+        }
+      }
+    }
+    if (lane == 0) fence_acq_rel_gpu();
+  }
+  __syncthreads();
 }
 
 #endif  // __CUDACC__

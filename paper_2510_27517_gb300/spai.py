@@ -59,7 +59,7 @@ class _Res(C.Structure):
 
 class _Sched(C.Structure):
     _fields_ = [("tile_nnz", C.c_int32), ("items_log2", C.c_int32), ("staged", C.c_int32), ("sell", C.c_int32),
-                ("tuned", C.c_int32)]
+                ("fuse", C.c_int32), ("tuned", C.c_int32)]
 
 
 class _ServeCfg(C.Structure):
@@ -264,8 +264,8 @@ class System(_Handle):
         _check(lib().spai_system_schedule(self.h, C.byref(sc)))
         return {k: getattr(sc, k) for k, _ in _Sched._fields_}
 
-    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1):
-        sc = _Sched(tile_nnz, items_log2, staged, sell, 0)
+    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1, fuse=1):
+        sc = _Sched(tile_nnz, items_log2, staged, sell, fuse, 0)
         _check(lib().spai_system_set_schedule(self.h, C.byref(sc)))
 
 

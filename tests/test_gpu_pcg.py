@@ -278,7 +278,8 @@ def test_autotuned_schedule_fixed_and_batch_consistent(spai_lib):
 
 
 @pytest.mark.parametrize("sched", [dict(sell=1), dict(sell=0, staged=1), dict(sell=0, staged=0),
-                                   dict(sell=1, tile_nnz=300, items_log2=2), dict(sell=0, tile_nnz=257, items_log2=-2)])
+                                   dict(sell=1, tile_nnz=300, items_log2=2), dict(sell=0, tile_nnz=257, items_log2=-2),
+                                   dict(sell=1, fuse=0), dict(sell=0, staged=0, fuse=0)])
 def test_every_schedule_matches_oracle(spai_lib, sched):
     # SELL-32 slices and CSR row groups (staged or direct), any group size:
     # the same float64 iteration as the oracle's Algorithm 1
@@ -315,7 +316,7 @@ def test_set_schedule_rejects_out_of_range(spai_lib):
     spai = spai_lib
     A = W.poisson2d(16)
     S = spai.system_create(upload(spai, A))
-    for bad in (dict(tile_nnz=5000), dict(items_log2=5), dict(staged=2), dict(sell=-1)):
+    for bad in (dict(tile_nnz=5000), dict(items_log2=5), dict(staged=2), dict(sell=-1), dict(fuse=2)):
         with pytest.raises(spai.SpaiError):
             S.set_schedule(**bad)
 
@@ -381,3 +382,73 @@ def test_host_buffer_solve_poisson64(spai_lib):
         x = x_h.numpy()
         assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
         assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x, b) <= 1e-8
+
+
+@pytest.mark.parametrize("case", ["gnn_sell_mixed", "gnn_csr_f64", "fsai_upper", "graph_direct", "batch"])
+def test_fused_step_is_bit_identical(spai_lib, case):
+    # the G^T and G passes in one grid step, ordered by item flags, run the
+    # same arithmetic as one grid step per pass: identical iterates, residual
+    # histories and iteration counts, for SELL-32 and CSR (staged and direct)
+    # layouts, a factor whose G and G^T have different row structure (FSAI on
+    # the upper triangle) and a batch
+    spai = spai_lib
+
+    def build(A, kind, seed):
+        dA = upload(spai, A)
+        if kind == "fsai":
+            M, _ = fsai_precond(spai, A, dA)
+            return dA, M, spai.PREC_F64
+        if kind == "gnn3d":
+            v = W.diffusion3d_node_features(kind_k[0])
+            P = spai.build_pattern(dA, spai.PATTERN_FULL)
+            mixed = case == "gnn_sell_mixed"
+            M = spai.gnn_precond(dA, P, torch.tensor(v, device="cuda"),
+                                 torch.tensor(W.gnn_random_weights(4, 4), device="cuda"), d_node=4,
+                                 g_dtype=spai.F32 if mixed else spai.F64, eps=0.3)
+            M._keep = P
+            return dA, M, spai.PREC_MIXED if mixed else spai.PREC_F64
+        P = spai.build_pattern(dA, spai.PATTERN_FULL)
+        M = spai.gnn_precond(dA, P, torch.tensor(W.row_average_feature(A), device="cuda"),
+                             torch.tensor(W.gnn_random_weights(1, 4), device="cuda"), d_node=1, g_dtype=spai.F32,
+                             eps=0.3)
+        M._keep = P
+        return dA, M, spai.PREC_MIXED
+
+    kind_k = [None]
+    if case in ("gnn_sell_mixed", "gnn_csr_f64"):
+        A, kind_k[0] = W.diffusion3d(16)
+        specs = [(A, "gnn3d", dict(sell=1) if case == "gnn_sell_mixed" else dict(sell=0, staged=1))]
+    elif case == "fsai_upper":
+        specs = [(W.poisson2d(48), "fsai", dict(sell=0, staged=1))]
+    elif case == "graph_direct":
+        specs = [(W.graph_laplacian(3000, 24000, seed=5), "graph", dict(sell=0, staged=0))]
+    else:
+        specs = [(W.graph_laplacian(2000, 16000, seed=6), "graph", dict(sell=0, staged=1)),
+                 (W.aniso2d(60, 30.0, 0.3), "graph", dict(sell=1)),
+                 (W.graph_laplacian(500, 4000, seed=7), "graph", dict(sell=0, staged=0))]
+    runs = {}
+    for fuse in (0, 1):
+        systems, preconds, bs, xs, hs, prec = [], [], [], [], [], None
+        for i, (A, kind, sched) in enumerate(specs):
+            dA, M, prec = build(A, kind, i)
+            S = spai.system_create(dA)
+            S.set_schedule(fuse=fuse, **sched)
+            systems.append(S), preconds.append(M)
+            bs.append(torch.tensor(W.rhs_uniform(A.n, 70 + i), device="cuda"))
+            xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+        if len(specs) == 1:
+            h = torch.zeros(100000, dtype=torch.float64, device="cuda")
+            r = [spai.system_solve(systems[0], preconds[0], bs[0], xs[0], history=h, precision=prec)]
+            hs = [h[:r[0]["history_written"]].clone()]
+        else:
+            r = spai.pcg_solve_batched(systems, preconds, bs, xs, precision=prec)
+        runs[fuse] = (r, [x.clone() for x in xs], hs)
+    (r0, x0, h0), (r1, x1, h1) = runs[0], runs[1]
+    for a, b in zip(r0, r1):
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["iters"] == b["iters"] and a["outer_iters"] == b["outer_iters"]
+        assert a["true_rel_res"] <= 1e-8
+    for a, b in zip(x0, x1):
+        assert torch.equal(a, b)
+    for a, b in zip(h0, h1):
+        assert torch.equal(a, b)
