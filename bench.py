@@ -765,7 +765,7 @@ def run_probe(args):
                          n_layers=4, g_dtype=spai.F32, eps=args.eps)
     x = torch.zeros(A_h.n, dtype=torch.float64, device="cuda")
     S = spai.system_create(A)
-    S.set_schedule(fuse=args.probe_fuse)
+    S.set_schedule(fuse=args.probe_fuse, items_log2=args.probe_klog)
     prec = spai.PREC_MIXED if args.precision == "mixed" else spai.PREC_F64
     if prec == spai.PREC_F64:
         M.close()
@@ -776,7 +776,7 @@ def run_probe(args):
     torch.cuda.synchronize()
     print(json.dumps({"probe": True, "n": A_h.n, "nnz": A_h.nnz, "iters": r["iters"], "engine_ms": r["engine_ms"],
                       "ms_per_iter": r["engine_ms"] / max(1, r["iters"]), "slots": r["slots"],
-                      "fuse": args.probe_fuse, "precision": args.precision}))
+                      "fuse": args.probe_fuse, "items_log2": args.probe_klog, "precision": args.precision}))
 
 
 # ---------------------------------------------------------------------------
@@ -846,6 +846,7 @@ def main():
     ap.add_argument("--chunk-iters", type=int, default=16)
     ap.add_argument("--probe", action="store_true", help="one short solve for profiler captures")
     ap.add_argument("--probe-iters", type=int, default=30)
+    ap.add_argument("--probe-klog", type=int, default=0, help="probe: groups per work item x 2^klog")
     ap.add_argument("--probe-fuse", type=int, default=1, choices=[0, 1],
                     help="probe: G^T and G passes in one grid step (1) or one step each (0)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
