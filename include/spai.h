@@ -263,6 +263,30 @@ int spai_gnn_precond(const spai_csr* A, const spai_pattern* P, const float* node
 int spai_gnn_grad(const spai_csr* A, const spai_pattern* P, const float* node_feat,
                   const spai_gnn_weights* W, const double* dG, double* dW, void* stream);
 
+/* One AdamW step for training the GNN's weights (Sec. 4.1 trains with AdamW
+ * and an exponentially decaying learning rate; decoupled weight decay as in
+ * Loshchilov & Hutter): with g = grad (scaled to 2-norm max_grad_norm first
+ * when it is larger and max_grad_norm > 0),
+ *   m = beta1 m + (1 - beta1) g,   v = beta2 v + (1 - beta2) g^2,
+ *   master -= lr (m / (1 - beta1^step) / (sqrt(v / (1 - beta2^step)) + eps)
+ *                 + weight_decay master),
+ * and blob = (float) master.  master, m, v, grad: device float64[count]
+ * (m and v start at zero, step counts from 1); blob: device float32[count]
+ * (the spai_gnn_weights blob).  *grad_norm (host, may be NULL) receives the
+ * gradient's 2-norm before clipping; then the call synchronises `stream`.
+ * SPAI_ERR_INVALID for a null pointer, count or step < 1 or a parameter out
+ * of range. */
+typedef struct {
+  double lr;             /* learning rate of this step */
+  double beta1, beta2;   /* moment decay rates (0.9, 0.999) */
+  double eps;            /* denominator guard (1e-8) */
+  double weight_decay;   /* decoupled decay rate (0.01) */
+  double max_grad_norm;  /* > 0: clip the gradient's 2-norm to this; <= 0: no clipping */
+} spai_adamw_cfg;
+
+int spai_adamw_step(double* master, double* m, double* v, const double* grad, float* blob, int64_t count,
+                    const spai_adamw_cfg* cfg, int64_t step, double* grad_norm, void* stream);
+
 /* Preconditioner from caller-supplied values of G on P (device array of
  * nnz_g values of type val_dtype, F64 or F32, in P's CSR order), stored in
  * g_dtype.  Used for classical factors (FSAI, Jacobi, identity). */
@@ -324,6 +348,22 @@ int spai_system_schedule(const spai_system* S, spai_schedule* out);
  * field out of range (tile_nnz above the largest group that fits the
  * staging buffer for this matrix, items_log2 outside -4..4, flags not 0/1). */
 int spai_system_set_schedule(spai_system* S, const spai_schedule* sch);
+
+/* Layout facts of a system (for callers and tests): sizes, the longest row,
+ * and the SELL-32 copy of A -- slices (0: none, CSR only), stored entries
+ * with padding, and whether its rows are ordered by length within windows
+ * of 1024 rows (SELL-C-sigma, chosen when rows in their own order would pad
+ * more than a quarter). */
+typedef struct {
+  int64_t n, nnz;
+  int32_t max_row;
+  int32_t sell_slices;
+  int64_t sell_total;
+  int32_t sell_sorted;
+  int32_t pad;
+} spai_system_layout;
+
+int spai_system_info(const spai_system* S, spai_system_layout* out);
 
 void spai_system_destroy(spai_system* S);
 

@@ -7,7 +7,7 @@ its Python binding.
 """
 from .spai import (  # noqa: F401
     BF16, CRIT_PRECOND, CRIT_RESIDUAL, F16, F32, F64, MSG_LATENT, MSG_RAW, PATTERN_FULL, PATTERN_LOWER,
-    PATTERN_UPPER, PREC_F64, PREC_MIXED, CSRMatrix, Pattern, Precond, Server, SpaiError, System, build_pattern,
+    PATTERN_UPPER, PREC_F64, PREC_MIXED, CSRMatrix, adamw_step, Pattern, Precond, Server, SpaiError, System, build_pattern,
     gnn_grad, gnn_precond, kernel_launches, lib, pcg_solve, pcg_solve_batched, pcg_solve_noalloc, pcg_solve_host, precond_from_values,
     ritz_extremes, ritz_kaporin, sai_loss, sai_loss_grad, selftest_wait_timeout, system_create, system_solve,
 )

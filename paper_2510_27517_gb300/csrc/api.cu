@@ -279,6 +279,19 @@ extern "C" int spai_system_schedule(const spai_system* S, spai_schedule* out) {
   return SPAI_OK;
 }
 
+extern "C" int spai_system_info(const spai_system* S, spai_system_layout* out) {
+  if (!S || !out) return set_error(SPAI_ERR_INVALID, "null argument");
+  const SystemData& d = *S->d;
+  memset(out, 0, sizeof(*out));
+  out->n = d.n;
+  out->nnz = d.nnz;
+  out->max_row = d.max_row;
+  out->sell_slices = d.sell_a.nslices;
+  out->sell_total = d.sell_a.total;
+  out->sell_sorted = d.sell_a.rows.p ? 1 : 0;
+  return SPAI_OK;
+}
+
 extern "C" int spai_system_set_schedule(spai_system* S, const spai_schedule* sch) {
   if (!S || !sch) return set_error(SPAI_ERR_INVALID, "null argument");
   SystemData& d = *S->d;

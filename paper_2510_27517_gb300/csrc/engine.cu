@@ -64,6 +64,7 @@ struct EngSys {
   int32_t fits[3];          // every group fits the stage buffer
   int32_t fmt[3];           // 0: CSR row groups (tiles = rows), 1: SELL-32 (tiles = slices)
   const int32_t* sptr[3];   // SELL-32 slice offsets (fmt 1)
+  const int32_t* srow[3];   // SELL-32 row at every slice position (rows sorted by length), or nullptr
   const int32_t* a_ci64;    // CSR column indices of A (float64 residual of mixed mode)
   int32_t nitems;           // work items of this system
   int32_t item_base;
@@ -503,7 +504,8 @@ template <int NS, class AT, class MV, class Op>
 __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict__ tiles,
                                              const int32_t* __restrict__ sptr, const int32_t* __restrict__ rp,
                                              const int32_t* ci, const MV* val, int g0, int g1, int64_t n,
-                                             const Op& op, double& p0, double& p1, uint64_t limit_ns, int* err) {
+                                             const Op& op, double& p0, double& p1, uint64_t limit_ns, int* err,
+                                             const int32_t* __restrict__ srow) {
   const int ng = g1 - g0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = kBlock / 32;
@@ -547,7 +549,7 @@ __device__ __forceinline__ void piped_slices(Pipe& P, const int32_t* __restrict_
         end = __ldg(sptr + sl + 1);
       }
       const int w = (end - off) >> 5;
-      const int row = sl * 32 + lane;
+      const int row = srow ? __ldg(srow + (size_t)sl * 32 + lane) : sl * 32 + lane;
       const bool valid = row < n;
       typename Op::Pre pr;
       if (valid) pr = op.pre(row);
@@ -615,9 +617,9 @@ template <class AT, bool CSR, class MV, class Op>
 __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* tiles, const int32_t* rp,
                                            const int32_t* ci, const MV* val, int g0, int g1, void* sbuf,
                                            double* red, const Op& op, double& p0, double& p1, uint64_t limit_ns,
-                                           int* err, const int32_t* sptr, int64_t n) {
+                                           int* err, const int32_t* sptr, int64_t n, const int32_t* srow) {
   if (sptr) piped_slices<(sizeof(AT) == 4 ? kStagesSell32 : kStages64), AT, MV>(P, tiles, sptr, rp, ci, val, g0, g1, n,
-                                                                          op, p0, p1, limit_ns, err);
+                                                                          op, p0, p1, limit_ns, err, srow);
   else if (CSR && piped) {
     if constexpr (CSR)
       piped_groups<(sizeof(AT) == 4 ? kStages32 : kStages64), AT, MV>(P, tiles, rp, ci, val, g0, g1, op, p0, p1,
@@ -650,37 +652,38 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   const int32_t* tl = S.tiles[m];
   const bool piped = S.fits[m] != 0;
   const int32_t* sp = S.fmt[m] ? S.sptr[m] : nullptr;  // SELL-32 slices
+  const int32_t* srow = S.fmt[m] ? S.srow[m] : nullptr;  // their rows, when sorted by length
   const int64_t n = S.n;
 
   switch (ph) {
     case PH_P1: {
       OpP1<VT> op{s, d_cur, d_nxt, q, beta, st.first != 0};
-      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_P2: {
       OpP2<VT> op{r_cur, r_nxt, q, d_cur, xv, t, alpha};
-      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_APPLY1: {
       OpApply1<VT> op{r_cur, t};
-      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_APPLY2: {
       OpApply2<VT> op{t, r_cur, s, eps};
-      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+      run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_RESID0:
     case PH_RESID: {
       if (!MIXED) {
         OpResid<VT> op{xv, S.b, r_cur};
-        run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+        run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       } else {
         OpResidIn<VT> op{xv, rin, r_cur};
-        run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n);
+        run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       }
       break;
     }
@@ -990,13 +993,20 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
 __global__ void deps_kernel(const int32_t* __restrict__ rp_c, const int32_t* __restrict__ ci_c,
                             const int32_t* __restrict__ tiles_c, int nt_c, int k_c, int sell_c,
                             const int32_t* __restrict__ tiles_p, int nt_p, int k_p, int sell_p, int nitems,
-                            int64_t n, int32_t* __restrict__ dep) {
+                            int64_t n, int32_t* __restrict__ dep, int all) {
   __shared__ int smin[kBlock / 32], smax[kBlock / 32];
   auto row_of = [n](const int32_t* tiles, int g, int sell) -> int64_t {
     const int64_t r = sell ? (int64_t)__ldg(tiles + g) * 32 : (int64_t)__ldg(tiles + g);
     return r < n ? r : n;
   };
   for (int v = blockIdx.x; v < nitems; v += gridDim.x) {
+    if (all) {
+      if (threadIdx.x == 0) {
+        dep[2 * v] = 0;
+        dep[2 * v + 1] = nitems - 1;
+      }
+      continue;
+    }
     const int g0 = v * k_c;
     const int g1 = min(g0 + k_c, nt_c);
     int lo = INT32_MAX, hi = -1;
@@ -1253,6 +1263,7 @@ class EngineBatch {
       if (sell_a) {
         e.fmt[MAT_A] = 1;
         e.sptr[MAT_A] = A.sell_a.sptr.as<int32_t>();
+        e.srow[MAT_A] = A.sell_a.row_map();
         e.ci[MAT_A] = A.sell_a.ci.as<int32_t>();
         e.val[MAT_A] = mixed_ ? (const void*)A.sell_v32.p : (const void*)A.sell_v64.p;
         if ((rc = build_tiles(e.sptr[MAT_A], A.sell_a.nslices, A.sell_a.total, sell_tile(A.sell_a.max_width),
@@ -1268,6 +1279,7 @@ class EngineBatch {
         const int32_t tg = sell_tile(L.max_width);
         e.fmt[MAT_GT] = e.fmt[MAT_G] = 1;
         e.sptr[MAT_GT] = e.sptr[MAT_G] = L.sptr.as<int32_t>();
+        e.srow[MAT_GT] = e.srow[MAT_G] = L.row_map();
         e.ci[MAT_GT] = e.ci[MAT_G] = L.ci.as<int32_t>();
         e.val[MAT_GT] = P.sell_gt.p;
         e.val[MAT_G] = P.sell_g.p;
@@ -1354,9 +1366,12 @@ class EngineBatch {
       e.dep = dep;
       const PrecondData& P = *members[i].M;
       const int dgrid = e.nitems < 4 * num_sms() ? e.nitems : 4 * num_sms();
+      // rows sorted by length within windows: an item's rows are no longer a
+      // contiguous range, so its G items wait for every G^T item
+      const int all = (e.srow[MAT_G] || e.srow[MAT_GT]) ? 1 : 0;
       deps_kernel<<<dgrid, kBlock, 0, s_>>>(P.P->g_rp(), P.P->g_ci(), e.tiles[MAT_G], e.ntiles[MAT_G],
                                             e.kgroups[MAT_G], e.fmt[MAT_G], e.tiles[MAT_GT], e.ntiles[MAT_GT],
-                                            e.kgroups[MAT_GT], e.fmt[MAT_GT], e.nitems, e.n, dep);
+                                            e.kgroups[MAT_GT], e.fmt[MAT_GT], e.nitems, e.n, dep, all);
       count_launch();
       SPAI_CUDA(cudaGetLastError());
     }

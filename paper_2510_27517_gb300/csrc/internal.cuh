@@ -52,19 +52,27 @@ size_t dtype_size(int dt);
 // ---------------------------------------------------------------------------
 // Handles
 // ---------------------------------------------------------------------------
-// SELL-32 layout of a CSR pattern: slices of 32 consecutive rows, each slice
-// stored column-major (entry k of the slice's 32 rows together) with the
-// width of its longest row.  Entry k of row i sits at
-// sptr[i / 32] + 32 k + i % 32; positions past a row's length are padding and
-// are never read.  Built only when every row has at most kSellMaxRow entries
-// and padding adds at most a quarter to the stored entries.
+// SELL-32 layout of a CSR pattern: slices of 32 rows, each slice stored
+// column-major (entry k of the slice's 32 rows together) with the width of
+// its longest row.  Entry k of the row at slice position p (slice p / 32,
+// lane p % 32) sits at sptr[p / 32] + 32 k + p % 32; positions past a row's
+// length are padding (column 0, value 0).  Plain SELL-32 keeps row i at
+// position i.  Where that pads more than a quarter (irregular rows), the
+// rows of every window of kSellSigma consecutive rows are ordered by
+// decreasing length (SELL-C-sigma; stable, so equal lengths keep their
+// order) and rows[p] holds the row at position p (n for the padding lanes
+// past the last row).  Built only when every row has at most kSellMaxRow
+// entries and the padding adds at most a quarter to the stored entries.
 constexpr int32_t kSellMaxRow = 64;
+constexpr int32_t kSellSigma = 1024;
 struct SellData {
   int32_t nslices = 0;         // 0: not available
   int32_t max_width = 0;
   int64_t total = 0;           // stored entries including padding
   DevMem sptr;                 // nslices + 1 entry offsets (multiples of 32)
   DevMem ci;                   // total column indices
+  DevMem rows;                 // 32 nslices row indices (sorted layout only; empty: row = position)
+  const int32_t* row_map() const { return rows.as<int32_t>(); }
 };
 
 struct PatternData {

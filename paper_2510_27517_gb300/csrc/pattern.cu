@@ -296,12 +296,18 @@ int system_from_csr(const spai_csr* A, SystemData& S, bool validate, cudaStream_
 }
 
 namespace {
+// Row at SELL position p: p itself, or the sorted layout's row map.
+__device__ __forceinline__ int64_t sell_row(const int32_t* __restrict__ rows, int64_t p) {
+  return rows ? (int64_t)rows[p] : p;
+}
+
 // 32 x (longest row) of every 32-row slice; one warp per slice
-__global__ void sell_width_kernel(const int32_t* __restrict__ rp, int64_t n, int64_t nslices, int32_t* w32) {
+__global__ void sell_width_kernel(const int32_t* __restrict__ rp, int64_t n, int64_t nslices, int32_t* w32,
+                                  const int32_t* __restrict__ rows) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nw) {
-    const int64_t row = sl * 32 + lane;
+    const int64_t row = sell_row(rows, sl * 32 + lane);
     int len = row < n ? rp[row + 1] - rp[row] : 0;
     for (int o = 16; o; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
     if (lane == 0) w32[sl] = 32 * len;
@@ -328,16 +334,41 @@ __device__ __forceinline__ void st_dt(void* p, int dt, int64_t i, double v) {
   }
 }
 
-// One thread per row (rows up to 32 * nslices): the row's column indices
-// (and values, when val is given) at their SELL positions, zeros in padding.
+// Row windows of kSellSigma rows, one thread each: the positions of the
+// window's rows ordered by decreasing length, rows of equal length in row
+// order (a stable counting sort over lengths 0..kSellMaxRow); positions past
+// the last row get n.
+__global__ void sell_sort_kernel(const int32_t* __restrict__ rp, int64_t n, int64_t npos, int32_t* __restrict__ rows) {
+  const int64_t nwin = (npos + kSellSigma - 1) / kSellSigma;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwin; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = w * kSellSigma;
+    const int64_t r1 = min(r0 + kSellSigma, n);
+    int cnt[kSellMaxRow + 1];
+    for (int l = 0; l <= kSellMaxRow; ++l) cnt[l] = 0;
+    for (int64_t r = r0; r < r1; ++r) cnt[rp[r + 1] - rp[r]]++;
+    int at[kSellMaxRow + 1];  // first position of each length, longest first
+    int acc = 0;
+    for (int l = kSellMaxRow; l >= 0; --l) {
+      at[l] = acc;
+      acc += cnt[l];
+    }
+    for (int64_t r = r0; r < r1; ++r) rows[r0 + at[rp[r + 1] - rp[r]]++] = (int32_t)r;
+    for (int64_t p = max(r1, r0); p < min(r0 + kSellSigma, npos); ++p) rows[p] = (int32_t)n;
+  }
+}
+
+// One thread per SELL position (32 * nslices): the column indices (and
+// values, when val is given) of the row there, zeros in padding.
 __global__ void sell_fill_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
                                  int64_t nslices, const int32_t* __restrict__ sptr, int32_t* ci_out,
-                                 const void* val, int dt_in, void* val_out, int dt_out) {
-  const int64_t rows = nslices * 32;
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < rows;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sl = row >> 5;
-    const int lane = (int)(row & 31);
+                                 const void* val, int dt_in, void* val_out, int dt_out,
+                                 const int32_t* __restrict__ rmap) {
+  const int64_t npos = nslices * 32;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npos;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = p >> 5;
+    const int lane = (int)(p & 31);
+    const int64_t row = sell_row(rmap, p);
     const int64_t off = sptr[sl];
     const int w = (sptr[sl + 1] - sptr[sl]) >> 5;
     const int64_t e0 = row < n ? rp[row] : 0;
@@ -355,34 +386,48 @@ int build_sell(const int32_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int
                cudaStream_t s) {
   out.nslices = 0;
   out.total = 0;
+  out.rows.release();
   if (n <= 0 || max_row < 1 || max_row > kSellMaxRow) return SPAI_OK;
   const int64_t ns = (n + 31) / 32;
   if ((int64_t)32 * max_row * ns >= (int64_t)INT32_MAX - 1024) return SPAI_OK;
   int rc;
   DevMem w;
   if ((rc = w.alloc((ns + 1) * sizeof(int32_t), s))) return rc;
-  SPAI_CUDA(cudaMemsetAsync(w.as<int32_t>() + ns, 0, sizeof(int32_t), s));
-  sell_width_kernel<<<grid_for(ns * 32, 256), 256, 0, s>>>(rp, n, ns, w.as<int32_t>()); count_launch();
-  SPAI_CUDA(cudaGetLastError());
   DevMem& sptr = out.sptr;
   if ((rc = sptr.alloc((ns + 1 + 16) * sizeof(int32_t), s))) return rc;
-  SPAI_CUDA(cudaMemsetAsync(sptr.p, 0, (ns + 1 + 16) * sizeof(int32_t), s));
-  if ((rc = exclusive_scan_i32(w.as<int32_t>(), sptr.as<int32_t>(), ns + 1, s))) return rc;
   int32_t total = 0;
-  SPAI_CUDA(cudaMemcpyAsync(&total, sptr.as<int32_t>() + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  SPAI_CUDA(cudaStreamSynchronize(s));
-  if ((int64_t)total * 4 > nnz * 5) {  // padding would add more than a quarter
-    sptr.release();
-    return SPAI_OK;
+  // rows in their own order first; if that pads more than a quarter, rows
+  // ordered by length within windows (SELL-C-sigma)
+  for (int sorted = 0; sorted < 2; ++sorted) {
+    if (sorted) {
+      if ((rc = out.rows.alloc((size_t)ns * 32 * sizeof(int32_t), s))) return rc;
+      const int64_t nwin = (ns * 32 + kSellSigma - 1) / kSellSigma;
+      sell_sort_kernel<<<grid_for(nwin, 128), 128, 0, s>>>(rp, n, ns * 32, out.rows.as<int32_t>()); count_launch();
+      SPAI_CUDA(cudaGetLastError());
+    }
+    SPAI_CUDA(cudaMemsetAsync(w.as<int32_t>() + ns, 0, sizeof(int32_t), s));
+    sell_width_kernel<<<grid_for(ns * 32, 256), 256, 0, s>>>(rp, n, ns, w.as<int32_t>(), out.row_map()); count_launch();
+    SPAI_CUDA(cudaGetLastError());
+    SPAI_CUDA(cudaMemsetAsync(sptr.p, 0, (ns + 1 + 16) * sizeof(int32_t), s));
+    if ((rc = exclusive_scan_i32(w.as<int32_t>(), sptr.as<int32_t>(), ns + 1, s))) return rc;
+    SPAI_CUDA(cudaMemcpyAsync(&total, sptr.as<int32_t>() + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA(cudaStreamSynchronize(s));
+    if ((int64_t)total * 4 <= nnz * 5) break;  // padding adds at most a quarter
+    if (sorted) {
+      sptr.release();
+      out.rows.release();
+      return SPAI_OK;
+    }
   }
   const int64_t pad = 64;
   if ((rc = out.ci.alloc((total + pad) * sizeof(int32_t), s))) return rc;
   SPAI_CUDA(cudaMemsetAsync(out.ci.p, 0, (total + pad) * sizeof(int32_t), s));
   sell_fill_kernel<<<grid_for(ns * 32, 256), 256, 0, s>>>(rp, ci, n, ns, sptr.as<int32_t>(), out.ci.as<int32_t>(),
-                                                          nullptr, 0, nullptr, 0); count_launch();
+                                                          nullptr, 0, nullptr, 0, out.row_map()); count_launch();
   SPAI_CUDA(cudaGetLastError());
   out.sptr.keep();
   out.ci.keep();
+  if (out.rows.p) out.rows.keep();
   out.nslices = (int32_t)ns;
   out.total = total;
   out.max_width = max_row;
@@ -393,7 +438,7 @@ int sell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val
                 cudaStream_t s) {
   if (L.nslices <= 0) return set_error(SPAI_ERR_INVALID, "no SELL layout");
   sell_fill_kernel<<<grid_for((int64_t)L.nslices * 32, 256), 256, 0, s>>>(
-      rp, nullptr, n, L.nslices, L.sptr.as<int32_t>(), nullptr, val, dt_in, out, dt_out); count_launch();
+      rp, nullptr, n, L.nslices, L.sptr.as<int32_t>(), nullptr, val, dt_in, out, dt_out, L.row_map()); count_launch();
   SPAI_CUDA(cudaGetLastError());
   return SPAI_OK;
 }

@@ -62,6 +62,16 @@ class _Sched(C.Structure):
                 ("fuse", C.c_int32), ("tuned", C.c_int32)]
 
 
+class _AdamW(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("weight_decay", C.c_double), ("max_grad_norm", C.c_double)]
+
+
+class _Layout(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int32), ("sell_slices", C.c_int32),
+                ("sell_total", C.c_int64), ("sell_sorted", C.c_int32), ("pad", C.c_int32)]
+
+
 class _ServeCfg(C.Structure):
     _fields_ = [("hbm_cap_bytes", C.c_int64), ("max_slots", C.c_int32), ("chunk_iters", C.c_int32),
                 ("opts", _Opts)]
@@ -96,6 +106,8 @@ _SIGS = {
                                 C.c_void_p, C.c_void_p]),
     "spai_gnn_precond": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.POINTER(_GNNW), C.c_int32,
                                    C.c_double, C.POINTER(C.c_void_p), C.c_void_p]),
+    "spai_adamw_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.POINTER(_AdamW), C.c_int64, C.POINTER(C.c_double), C.c_void_p]),
     "spai_precond_from_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
                                            C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_precond_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
@@ -104,6 +116,7 @@ _SIGS = {
     "spai_system_create": (C.c_int, [C.POINTER(_CSR), C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
     "spai_system_schedule": (C.c_int, [C.c_void_p, C.POINTER(_Sched)]),
     "spai_system_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(_Sched)]),
+    "spai_system_info": (C.c_int, [C.c_void_p, C.POINTER(_Layout)]),
     "spai_system_destroy": (None, [C.c_void_p]),
     "spai_pcg_solve": (C.c_int, [C.POINTER(_CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts),
                                  C.POINTER(_Res), C.c_void_p]),
@@ -264,6 +277,11 @@ class System(_Handle):
         _check(lib().spai_system_schedule(self.h, C.byref(sc)))
         return {k: getattr(sc, k) for k, _ in _Sched._fields_}
 
+    def layout(self):
+        lo = _Layout()
+        _check(lib().spai_system_info(self.h, C.byref(lo)))
+        return {k: getattr(lo, k) for k, _ in _Layout._fields_ if k != "pad"}
+
     def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1, fuse=1):
         sc = _Sched(tile_nnz, items_log2, staged, sell, fuse, 0)
         _check(lib().spai_system_set_schedule(self.h, C.byref(sc)))
@@ -303,6 +321,22 @@ def gnn_grad(A: CSRMatrix, P: Pattern, node_feat: torch.Tensor, blob: torch.Tens
     _check(lib().spai_gnn_grad(C.byref(A._c()), P.h, _ptr(node_feat), C.byref(w), _ptr(dG), _ptr(out),
                                _stream(stream)))
     return out
+
+
+def adamw_step(master: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, blob: torch.Tensor,
+               step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01, max_grad_norm=0.0,
+               stream=None) -> float:
+    """One AdamW step (spai_adamw_step) on the float64 master weights, moments
+    m and v, writing the float32 blob; returns the gradient's 2-norm."""
+    count = master.numel()
+    for t in (master, m, v, grad):
+        _check_vec(t, count, "AdamW state")
+    assert blob.dtype == torch.float32 and blob.is_cuda and blob.is_contiguous() and blob.numel() == count
+    cfg = _AdamW(lr, beta1, beta2, eps, weight_decay, max_grad_norm)
+    gn = C.c_double()
+    _check(lib().spai_adamw_step(_ptr(master), _ptr(m), _ptr(v), _ptr(grad), _ptr(blob), count, C.byref(cfg), step,
+                                 C.byref(gn), _stream(stream)))
+    return gn.value
 
 
 def precond_from_values(P: Pattern, g_val: torch.Tensor, g_dtype=F64, eps=0.0, stream=None) -> Precond:

@@ -279,20 +279,35 @@ def test_autotuned_schedule_fixed_and_batch_consistent(spai_lib):
 
 @pytest.mark.parametrize("sched", [dict(sell=1), dict(sell=0, staged=1), dict(sell=0, staged=0),
                                    dict(sell=1, tile_nnz=300, items_log2=2), dict(sell=0, tile_nnz=257, items_log2=-2),
-                                   dict(sell=1, fuse=0), dict(sell=0, staged=0, fuse=0)])
+                                   dict(sell=1, fuse=0), dict(sell=0, staged=0, fuse=0),
+                                   dict(matrix="graph", sell=1), dict(matrix="graph", sell=1, fuse=0),
+                                   dict(matrix="graph", sell=1, tile_nnz=300, items_log2=1),
+                                   dict(matrix="graph", sell=0, staged=1)])
 def test_every_schedule_matches_oracle(spai_lib, sched):
-    # SELL-32 slices and CSR row groups (staged or direct), any group size:
-    # the same float64 iteration as the oracle's Algorithm 1
+    # SELL-32 slices (rows in their own order for the stencil; ordered by
+    # length within windows for the graph Laplacian, whose rows are too
+    # uneven for plain slices) and CSR row groups (staged or direct), any
+    # group size: the same float64 iteration as the oracle's Algorithm 1
     spai = spai_lib
-    A, k = W.diffusion3d(12)
-    v = W.diffusion3d_node_features(k)
+    sched = dict(sched)
+    graph = sched.pop("matrix", "stencil") == "graph"
+    if graph:
+        A = W.graph_laplacian(3000, 24000, seed=13)
+        v, d_node = W.row_average_feature(A), 1
+    else:
+        A, k = W.diffusion3d(12)
+        v, d_node = W.diffusion3d_node_features(k), 4
     dA = upload(spai, A)
     S = spai.system_create(dA)
+    lay = S.layout()
+    assert lay["sell_slices"] > 0 and lay["sell_sorted"] == (1 if graph else 0)
+    assert lay["sell_total"] * 4 <= A.nnz * 5
     S.set_schedule(**sched)
     assert S.schedule()["tuned"] == 1
     P = spai.build_pattern(dA, spai.PATTERN_FULL)
     M = spai.gnn_precond(dA, P, torch.tensor(v, device="cuda"),
-                         torch.tensor(W.gnn_random_weights(4, 4), device="cuda"), d_node=4, g_dtype=spai.F64, eps=0.3)
+                         torch.tensor(W.gnn_random_weights(d_node, 4), device="cuda"), d_node=d_node,
+                         g_dtype=spai.F64, eps=0.3)
     g, _ = M.export(spai.F64)
     b = W.rhs_uniform(A.n, 31)
     ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, A.rowptr, A.colidx, g.cpu().numpy(), 0.3),
@@ -425,7 +440,8 @@ def test_fused_step_is_bit_identical(spai_lib, case):
     else:
         specs = [(W.graph_laplacian(2000, 16000, seed=6), "graph", dict(sell=0, staged=1)),
                  (W.aniso2d(60, 30.0, 0.3), "graph", dict(sell=1)),
-                 (W.graph_laplacian(500, 4000, seed=7), "graph", dict(sell=0, staged=0))]
+                 (W.graph_laplacian(500, 4000, seed=7), "graph", dict(sell=0, staged=0)),
+                 (W.graph_laplacian(4000, 32000, seed=8), "graph", dict(sell=1))]
     runs = {}
     for fuse in (0, 1):
         systems, preconds, bs, xs, hs, prec = [], [], [], [], [], None
