@@ -315,6 +315,10 @@ void spai_precond_destroy(spai_precond* M);
  *               padding adds at most 25%) are read in that layout, one row
  *               per lane; 0: CSR row groups.  The group size of the SELL
  *               layout scales with tile_nnz.
+ *   block       1: a matrix made of dense 3 x 3 blocks (A, and G on its
+ *               pattern) is read in the 3 x 3 block layout: slices of 32 block
+ *               rows, one column index per block and its 9 values, a lane
+ *               per block row (three scalar rows); 0: scalar layouts.
  *   fuse        1: the G^T and G passes of an iteration run in one grid-wide
  *               step, a G work item starting once the G^T items whose rows
  *               it reaches have finished (per-item flags instead of a
@@ -338,6 +342,8 @@ typedef struct {
   int32_t staged;      /* 0 or 1 */
   int32_t sell;        /* 1: SELL-32 layout for the matrices that have one, 0: CSR row groups */
   int32_t fuse;        /* 1: G^T and G passes in one grid-wide step (default), 0: separate steps */
+  int32_t block;       /* 1: the 3 x 3 block layout for A, G and G^T when they are made of dense 3 x 3
+                          blocks (default), 0: scalar layouts */
   int32_t tuned;       /* out: 1 once the autotuner ran or a schedule was set */
 } spai_schedule;
 
@@ -350,17 +356,19 @@ int spai_system_schedule(const spai_system* S, spai_schedule* out);
 int spai_system_set_schedule(spai_system* S, const spai_schedule* sch);
 
 /* Layout facts of a system (for callers and tests): sizes, the longest row,
- * and the SELL-32 copy of A -- slices (0: none, CSR only), stored entries
- * with padding, and whether its rows are ordered by length within windows
- * of 1024 rows (SELL-C-sigma, chosen when rows in their own order would pad
- * more than a quarter). */
+ * the SELL-32 copy of A -- slices (0: none, CSR only), stored entries with
+ * padding, and whether its rows are ordered by length within windows of
+ * 1024 rows (SELL-C-sigma, chosen when rows in their own order would pad
+ * more than a quarter) -- and the 3 x 3 block copy (slices of 32 block rows;
+ * 0 when A is not made of dense 3 x 3 blocks; stored blocks with padding). */
 typedef struct {
   int64_t n, nnz;
   int32_t max_row;
   int32_t sell_slices;
   int64_t sell_total;
   int32_t sell_sorted;
-  int32_t pad;
+  int32_t block_slices;
+  int64_t block_total;
 } spai_system_layout;
 
 int spai_system_info(const spai_system* S, spai_system_layout* out);

@@ -252,6 +252,22 @@ int make_system(const spai_csr* A, int autotune, std::shared_ptr<SystemData>& ou
     S->sell_v64.keep();
     S->sell_v32.keep();
   }
+  if ((rc = build_bsell(S->rowptr.as<int32_t>(), S->colidx.as<int32_t>(), S->n, S->nnz, S->bsell_a, s))) return rc;
+  if (S->bsell_a.nslices > 0) {
+    const size_t tot = (size_t)9 * S->bsell_a.total + 64;
+    if ((rc = S->bsell_v64.alloc(tot * sizeof(double), s))) return rc;
+    if ((rc = S->bsell_v32.alloc(tot * sizeof(float), s))) return rc;
+    SPAI_CUDA(cudaMemsetAsync(S->bsell_v64.p, 0, tot * sizeof(double), s));
+    SPAI_CUDA(cudaMemsetAsync(S->bsell_v32.p, 0, tot * sizeof(float), s));
+    if ((rc = bsell_values(S->bsell_a, S->rowptr.as<int32_t>(), S->n, S->val64.p, SPAI_F64, S->bsell_v64.p, SPAI_F64,
+                           s)))
+      return rc;
+    if ((rc = bsell_values(S->bsell_a, S->rowptr.as<int32_t>(), S->n, S->val64.p, SPAI_F64, S->bsell_v32.p, SPAI_F32,
+                           s)))
+      return rc;
+    S->bsell_v64.keep();
+    S->bsell_v32.keep();
+  }
   out = S;
   return SPAI_OK;
 }
@@ -275,6 +291,7 @@ extern "C" int spai_system_schedule(const spai_system* S, spai_schedule* out) {
   out->staged = S->d->staged;
   out->sell = S->d->sell;
   out->fuse = S->d->fuse;
+  out->block = S->d->block;
   out->tuned = S->d->tuned;
   return SPAI_OK;
 }
@@ -289,6 +306,8 @@ extern "C" int spai_system_info(const spai_system* S, spai_system_layout* out) {
   out->sell_slices = d.sell_a.nslices;
   out->sell_total = d.sell_a.total;
   out->sell_sorted = d.sell_a.rows.p ? 1 : 0;
+  out->block_slices = d.bsell_a.nslices;
+  out->block_total = d.bsell_a.total;
   return SPAI_OK;
 }
 
@@ -300,13 +319,14 @@ extern "C" int spai_system_set_schedule(spai_system* S, const spai_schedule* sch
     return set_error(SPAI_ERR_INVALID, "tile_nnz must be in 1..%d (0: default)", (int)t0);
   if (sch->items_log2 < -4 || sch->items_log2 > 4) return set_error(SPAI_ERR_INVALID, "items_log2 must be in -4..4");
   if ((sch->staged != 0 && sch->staged != 1) || (sch->sell != 0 && sch->sell != 1) ||
-      (sch->fuse != 0 && sch->fuse != 1))
-    return set_error(SPAI_ERR_INVALID, "staged, sell and fuse must be 0 or 1");
+      (sch->fuse != 0 && sch->fuse != 1) || (sch->block != 0 && sch->block != 1))
+    return set_error(SPAI_ERR_INVALID, "staged, sell, fuse and block must be 0 or 1");
   d.tile_nnz = sch->tile_nnz ? sch->tile_nnz : t0;
   d.items_log2 = sch->items_log2;
   d.staged = sch->staged;
   d.sell = sch->sell;
   d.fuse = sch->fuse;
+  d.block = sch->block;
   d.tuned = 1;
   return SPAI_OK;
 }

@@ -62,7 +62,8 @@ struct EngSys {
   int32_t ntiles[3];        // groups per matrix
   int32_t kgroups[3];       // groups per work item per matrix
   int32_t fits[3];          // every group fits the stage buffer
-  int32_t fmt[3];           // 0: CSR row groups (tiles = rows), 1: SELL-32 (tiles = slices)
+  int32_t fmt[3];           // 0: CSR row groups (tiles = rows), 1: SELL-32 (tiles = slices),
+                            // 2: 3 x 3 blocks (tiles = slices of 32 block rows)
   const int32_t* sptr[3];   // SELL-32 slice offsets (fmt 1)
   const int32_t* srow[3];   // SELL-32 row at every slice position (rows sorted by length), or nullptr
   const int32_t* a_ci64;    // CSR column indices of A (float64 residual of mixed mode)
@@ -610,6 +611,71 @@ __device__ __noinline__ double2 direct_rows(const int32_t* __restrict__ rp, cons
   return make_double2(p0, p1);
 }
 
+// Rows covered by one tile unit of a format: a CSR row, a 32-row slice, or a
+// slice of 32 block rows (96 scalar rows).
+__host__ __device__ __forceinline__ int rows_per_unit(int fmt) { return fmt == 1 ? 32 : (fmt == 2 ? 96 : 1); }
+
+// Slices [tiles[g0], tiles[g1]) of the 3 x 3 block layout (bsell.cu), direct
+// loads: a warp per slice (slices dealt to warps round-robin), a lane per
+// block row I (scalar rows 3I .. 3I + 2).  Per block: its column J, the three
+// gathers at 3J .. 3J + 2 and its 9 values; each scalar row sums its entries
+// in stored order (blocks in column order, columns within a block in order),
+// the per-row arithmetic of the scalar layouts.  Two blocks are in flight per
+// step.  Not inlined (its registers stay out of the scalar paths).
+template <class AT, class MV, class Op>
+__device__ __noinline__ double2 direct_bslices(const int32_t* __restrict__ tiles, const int32_t* __restrict__ sptr,
+                                               const int32_t* __restrict__ ci, const MV* __restrict__ val, int g0,
+                                               int g1, int64_t n, const Op op) {
+  constexpr int NW = kBlock / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double p0 = 0.0, p1 = 0.0;
+  const int s0 = __ldg(tiles + g0), s1 = __ldg(tiles + g1);
+  for (int sl = s0 + warp; sl < s1; sl += NW) {
+    const int off = __ldg(sptr + sl);
+    const int w = (__ldg(sptr + sl + 1) - off) >> 5;
+    const int64_t row0 = 3 * ((int64_t)sl * 32 + lane);
+    const bool valid = row0 < n;
+    typename Op::Pre pr[3];
+    if (valid) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) pr[r] = op.pre((int)row0 + r);
+    }
+    AT acc[3] = {AT(0), AT(0), AT(0)};
+    const int32_t* cl = ci + off + lane;
+    const MV* vl = val + 9 * (size_t)off + lane;
+    for (int q = 0; q < w; q += 2) {
+      const bool two = q + 1 < w;
+      const int j0 = __ldg(cl + 32 * q);
+      const int j1 = two ? __ldg(cl + 32 * (q + 1)) : 0;
+      AT v0[9], v1[9], x0[3], x1[3];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        v0[k] = Conv<AT>::f(ldro(vl + 32 * (9 * q + k)));
+        v1[k] = two ? Conv<AT>::f(ldro(vl + 32 * (9 * (q + 1) + k))) : AT(0);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x0[c] = op.gather(3 * j0 + c);
+        x1[c] = two ? op.gather(3 * j1 + c) : AT(0);
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[r] = rfma(v0[3 * r + c], x0[c], acc[r]);
+        if (two) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[r] = rfma(v1[3 * r + c], x1[c], acc[r]);
+        }
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) op.fin((int)row0 + r, acc[r], pr[r], p0, p1);
+    }
+  }
+  return make_double2(p0, p1);
+}
+
 // CSR: the kernel streams CSR groups through the ring; kernels for launches
 // without such groups (every member SELL-32 or direct) leave that code out,
 // which keeps the SELL-32 loop free of its register pressure.
@@ -639,7 +705,7 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   VT* r_nxt = reinterpret_cast<VT*>(S.r[rc ^ 1]);
   VT* d_cur = reinterpret_cast<VT*>(S.d[dc]);
   VT* d_nxt = reinterpret_cast<VT*>(S.d[dc ^ 1]);
-  VT* q = reinterpret_cast<VT*>(S.q);
+  VT* q_v = reinterpret_cast<VT*>(S.q);
   VT* t = reinterpret_cast<VT*>(S.t);
   VT* s = reinterpret_cast<VT*>(S.s);
   VT* xv = MIXED ? reinterpret_cast<VT*>(S.e) : reinterpret_cast<VT*>(S.x);  // iterate
@@ -651,18 +717,50 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   const int m = phase_mat(ph);
   const int32_t* tl = S.tiles[m];
   const bool piped = S.fits[m] != 0;
-  const int32_t* sp = S.fmt[m] ? S.sptr[m] : nullptr;  // SELL-32 slices
-  const int32_t* srow = S.fmt[m] ? S.srow[m] : nullptr;  // their rows, when sorted by length
+  const int32_t* sp = S.fmt[m] == 1 ? S.sptr[m] : nullptr;  // SELL-32 slices
+  const int32_t* srow = S.fmt[m] == 1 ? S.srow[m] : nullptr;  // their rows, when sorted by length
   const int64_t n = S.n;
+  const int rpu = rows_per_unit(S.fmt[m]);
+  // 3 x 3 block layout: compiled into the full kernel only (launches with a
+  // block member run it), so the SELL-32 kernel keeps its registers
+  if (CSR && S.fmt[m] == 2 && ph != PH_RESID64 && ph != PH_P2X && ph != PH_XUPD && ph != PH_ZEROX) {
+    double2 q = make_double2(0.0, 0.0);
+    if constexpr (CSR) switch (ph) {
+      case PH_P1:
+        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n,
+                               OpP1<VT>{s, d_cur, d_nxt, q_v, beta, st.first != 0});
+        break;
+      case PH_P2:
+        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_GT], gtval, g0, g1, n,
+                               OpP2<VT>{r_cur, r_nxt, q_v, d_cur, xv, t, alpha});
+        break;
+      case PH_APPLY1:
+        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_GT], gtval, g0, g1, n, OpApply1<VT>{r_cur, t});
+        break;
+      case PH_APPLY2:
+        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_G], gval, g0, g1, n, OpApply2<VT>{t, r_cur, s, eps});
+        break;
+      case PH_RESID0:
+      case PH_RESID:
+        if (!MIXED) q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n, OpResid<VT>{xv, S.b, r_cur});
+        else q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n, OpResidIn<VT>{xv, rin, r_cur});
+        break;
+      default:
+        break;
+    }
+    p0 += q.x;
+    p1 += q.y;
+    return;
+  }
 
   switch (ph) {
     case PH_P1: {
-      OpP1<VT> op{s, d_cur, d_nxt, q, beta, st.first != 0};
+      OpP1<VT> op{s, d_cur, d_nxt, q_v, beta, st.first != 0};
       run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_P2: {
-      OpP2<VT> op{r_cur, r_nxt, q, d_cur, xv, t, alpha};
+      OpP2<VT> op{r_cur, r_nxt, q_v, d_cur, xv, t, alpha};
       run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
@@ -690,8 +788,8 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
     case PH_RESID64: {
       if constexpr (MIXED) {
         OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
-        if (sp) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
-          const int r0 = __ldg(tl + g0) * 32, r1 = (int)min((int64_t)__ldg(tl + g1) * 32, n);
+        if (rpu > 1) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
+          const int r0 = __ldg(tl + g0) * rpu, r1 = (int)min((int64_t)__ldg(tl + g1) * rpu, n);
           if (r0 < r1) {
             const double2 q =
                 direct_rows<double>(S.rp[MAT_A], S.a_ci64, S.a_v64, r0, r1, reinterpret_cast<double*>(sbuf), red, op);
@@ -710,8 +808,8 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
     case PH_P2X:
     case PH_XUPD:
     case PH_ZEROX: {
-      const int r0 = sp ? __ldg(tl + g0) * 32 : __ldg(tl + g0);
-      const int r1 = sp ? (int)min((int64_t)__ldg(tl + g1) * 32, n) : __ldg(tl + g1);
+      const int r0 = __ldg(tl + g0) * rpu;
+      const int r1 = (int)min((int64_t)__ldg(tl + g1) * rpu, n);
       for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
         if (ph == PH_P2X) xv[row] = rfma(alpha, ldv(d_cur + row), ldv(xv + row));
         else if (ph == PH_XUPD) {
@@ -991,12 +1089,12 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
 // item's CSR entries, then the producer items by binary search over their
 // first rows.  Rows come in CSR row groups (sell 0) or 32-row slices (sell 1).
 __global__ void deps_kernel(const int32_t* __restrict__ rp_c, const int32_t* __restrict__ ci_c,
-                            const int32_t* __restrict__ tiles_c, int nt_c, int k_c, int sell_c,
-                            const int32_t* __restrict__ tiles_p, int nt_p, int k_p, int sell_p, int nitems,
+                            const int32_t* __restrict__ tiles_c, int nt_c, int k_c, int fmt_c,
+                            const int32_t* __restrict__ tiles_p, int nt_p, int k_p, int fmt_p, int nitems,
                             int64_t n, int32_t* __restrict__ dep, int all) {
   __shared__ int smin[kBlock / 32], smax[kBlock / 32];
-  auto row_of = [n](const int32_t* tiles, int g, int sell) -> int64_t {
-    const int64_t r = sell ? (int64_t)__ldg(tiles + g) * 32 : (int64_t)__ldg(tiles + g);
+  auto row_of = [n](const int32_t* tiles, int g, int fmt) -> int64_t {
+    const int64_t r = (int64_t)__ldg(tiles + g) * rows_per_unit(fmt);
     return r < n ? r : n;
   };
   for (int v = blockIdx.x; v < nitems; v += gridDim.x) {
@@ -1011,7 +1109,7 @@ __global__ void deps_kernel(const int32_t* __restrict__ rp_c, const int32_t* __r
     const int g1 = min(g0 + k_c, nt_c);
     int lo = INT32_MAX, hi = -1;
     if (g0 < g1) {
-      const int64_t r0 = row_of(tiles_c, g0, sell_c), r1 = row_of(tiles_c, g1, sell_c);
+      const int64_t r0 = row_of(tiles_c, g0, fmt_c), r1 = row_of(tiles_c, g1, fmt_c);
       if (r0 < r1) {
         const int64_t e0 = __ldg(rp_c + r0), e1 = __ldg(rp_c + r1);
         for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -1043,7 +1141,7 @@ __global__ void deps_kernel(const int32_t* __restrict__ rp_c, const int32_t* __r
           while (a < b) {
             const int mid = (a + b + 1) >> 1;
             const int g = min(mid * k_p, nt_p);
-            if (row_of(tiles_p, g, sell_p) <= c) a = mid; else b = mid - 1;
+            if (row_of(tiles_p, g, fmt_p) <= c) a = mid; else b = mid - 1;
           }
           return a;
         };
@@ -1251,8 +1349,13 @@ class EngineBatch {
       // SELL-32 where the matrix has the layout and the schedule asks for it
       // (all three share one choice, so a system's arithmetic depends on its
       // schedule only); the group size scales like the CSR one
-      const bool sell_a = A.sell && A.sell_a.nslices > 0 && A.sell_v64.p;
-      const bool sell_g = A.sell && P.P->sell.nslices > 0 && P.sell_g.p && P.sell_gt.p;
+      // the 3 x 3 block layout where A (and G on its pattern) have it and the
+      // schedule asks for it, else SELL-32, else CSR row groups
+      const bool blk_a = A.block && A.bsell_a.nslices > 0 && A.bsell_v64.p;
+      const bool blk_g = A.block && P.P->bsell.nslices > 0 && P.bsell_g.p && P.bsell_gt.p;
+      const bool sell_a = !blk_a && A.sell && A.sell_a.nslices > 0 && A.sell_v64.p;
+      const bool sell_g = !blk_g && A.sell && P.P->sell.nslices > 0 && P.sell_g.p && P.sell_gt.p;
+      const int32_t tblk = (tn + 8) / 9 > 1 ? (tn + 8) / 9 : 1;  // blocks per group (about tn values)
       const int32_t t0 = engine_tile_nnz(A.max_row);
       auto sell_tile = [&](int32_t width) {
         const int64_t tmax = (int64_t)kCap + 1 - 32 * (int64_t)width;
@@ -1260,7 +1363,13 @@ class EngineBatch {
         if (t > tmax) t = tmax;
         return (int32_t)(t < 1 ? 1 : t);
       };
-      if (sell_a) {
+      if (blk_a) {
+        e.fmt[MAT_A] = 2;
+        e.sptr[MAT_A] = A.bsell_a.sptr.as<int32_t>();
+        e.ci[MAT_A] = A.bsell_a.ci.as<int32_t>();
+        e.val[MAT_A] = mixed_ ? (const void*)A.bsell_v32.p : (const void*)A.bsell_v64.p;
+        if ((rc = build_tiles(e.sptr[MAT_A], A.bsell_a.nslices, A.bsell_a.total, tblk, A.tiles, s_))) return rc;
+      } else if (sell_a) {
         e.fmt[MAT_A] = 1;
         e.sptr[MAT_A] = A.sell_a.sptr.as<int32_t>();
         e.srow[MAT_A] = A.sell_a.row_map();
@@ -1274,7 +1383,16 @@ class EngineBatch {
         e.val[MAT_A] = mixed_ ? (const void*)A.val32.p : (const void*)A.val64.p;
         if ((rc = build_tiles(A.rowptr.as<int32_t>(), A.n, A.nnz, tn, A.tiles, s_))) return rc;
       }
-      if (sell_g) {
+      if (blk_g) {
+        const SellData& L = P.P->bsell;
+        e.fmt[MAT_GT] = e.fmt[MAT_G] = 2;
+        e.sptr[MAT_GT] = e.sptr[MAT_G] = L.sptr.as<int32_t>();
+        e.ci[MAT_GT] = e.ci[MAT_G] = L.ci.as<int32_t>();
+        e.val[MAT_GT] = P.bsell_gt.p;
+        e.val[MAT_G] = P.bsell_g.p;
+        if ((rc = build_tiles(L.sptr.as<int32_t>(), L.nslices, L.total, tblk, P.gt_tiles, s_))) return rc;
+        if ((rc = build_tiles(L.sptr.as<int32_t>(), L.nslices, L.total, tblk, P.g_tiles, s_))) return rc;
+      } else if (sell_g) {
         const SellData& L = P.P->sell;
         const int32_t tg = sell_tile(L.max_width);
         e.fmt[MAT_GT] = e.fmt[MAT_G] = 1;
@@ -1303,7 +1421,7 @@ class EngineBatch {
       for (int mm = 0; mm < 3; ++mm) {
         e.fits[mm] = e.fmt[mm] ? 1 : fits;
         if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
-        if (!e.fmt[mm] && e.fits[mm]) csr_ring = true;
+        if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2) csr_ring = true;  // the full kernel
       }
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
@@ -1681,17 +1799,17 @@ __global__ void tune_rhs_kernel(double* b, double* x, int64_t n) {
 int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
   constexpr int kTuneIters = 12;
   const int32_t t0 = engine_tile_nnz(S->max_row);
-  struct Cand { int32_t tile, klog, staged, sell, fuse; };
+  struct Cand { int32_t tile, klog, staged, sell, fuse, block; };
   std::vector<Cand> cands;
   const bool has_sell = S->sell_a.nslices > 0 || M->P->sell.nslices > 0;
   for (int div : {1, 2, 4}) {
     const int32_t t = t0 / div;
     if (div > 1 && t < 256) continue;
     for (int kl : {0, -1, 1}) {
-      if (has_sell) cands.push_back(Cand{t, kl, 1, 1, 1});
+      if (has_sell) cands.push_back(Cand{t, kl, 1, 1, 1, 1});
       for (int st : {1, 0}) {
         if (st == 0 && !engine_groups_fit(S->max_row)) continue;  // direct loads either way
-        cands.push_back(Cand{t, kl, st, 0, 1});
+        cands.push_back(Cand{t, kl, st, 0, 1, 1});
       }
     }
   }
@@ -1699,6 +1817,18 @@ int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
     Cand c = cands[0];  // the heuristic schedule with one grid step per pass
     c.fuse = 0;
     cands.push_back(c);
+  }
+  // systems made of 3 x 3 blocks: the block layout (default) against the scalar ones
+  const bool has_blk = S->bsell_a.nslices > 0 || M->P->bsell.nslices > 0;
+  for (Cand& c : cands) c.block = 1;
+  if (has_blk) {
+    const size_t nc = cands.size();
+    for (size_t i = 0; i < nc; ++i)
+      if (cands[i].tile == t0 && cands[i].fuse) {
+        Cand c = cands[i];
+        c.block = 0;
+        cands.push_back(c);
+      }
   }
   DevMem buf;
   int rc;
@@ -1719,6 +1849,7 @@ int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
     S->staged = c.staged;
     S->sell = c.sell;
     S->fuse = c.fuse;
+    S->block = c.block;
     double t = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
       tune_rhs_kernel<<<256, 256, 0, s>>>(b, x, S->n);
@@ -1741,6 +1872,7 @@ int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
   S->staged = best.staged;
   S->sell = best.sell;
   S->fuse = best.fuse;
+  S->block = best.block;
   S->tuned = 1;
   set_error(SPAI_OK, "no error");
   return SPAI_OK;

@@ -68,6 +68,7 @@ constexpr int32_t kSellSigma = 1024;
 struct SellData {
   int32_t nslices = 0;         // 0: not available
   int32_t max_width = 0;
+  int32_t block = 1;           // 3: the 3 x 3 block layout of bsell.cu (entries and widths count blocks)
   int64_t total = 0;           // stored entries including padding
   DevMem sptr;                 // nslices + 1 entry offsets (multiples of 32)
   DevMem ci;                   // total column indices
@@ -86,6 +87,7 @@ struct PatternData {
   DevMem src;                  // index into A of each entry of G (LOWER/UPPER only)
   int64_t a_nnz = 0;           // nnz of the A it was built from
   SellData sell;               // FULL patterns (shared by G and G^T)
+  SellData bsell;              // FULL patterns made of dense 3 x 3 blocks
   const int32_t* g_rp() const { return rowptr.as<int32_t>(); }
   const int32_t* g_ci() const { return colidx.as<int32_t>(); }
   const int32_t* gt_rp() const { return kind == SPAI_PATTERN_FULL ? rowptr.as<int32_t>() : t_rowptr.as<int32_t>(); }
@@ -109,6 +111,7 @@ struct PrecondData {
   double anorm = 0.0;        // ||A|| used by the GNN (0 when values were given)
   DevMem g_val, gt_val;
   DevMem sell_g, sell_gt;    // values in the pattern's SELL-32 layout (when it has one)
+  DevMem bsell_g, bsell_gt;  // values in the pattern's 3 x 3 block layout (when it has one)
   TileSet g_tiles, gt_tiles; // cached for the last tile size used
 };
 
@@ -122,11 +125,14 @@ struct SystemData {
   int32_t staged = 1;        // 1: groups staged by TMA bulk copies (when rows fit), 0: direct loads
   int32_t sell = 1;          // 1: SELL-32 layout for matrices that have one, 0: CSR row groups
   int32_t fuse = 1;          // 1: G^T and G passes in one grid step ordered by item flags
+  int32_t block = 1;         // 1: the 3 x 3 block layout for matrices that have it (A and G)
   int32_t autotune = 0;      // pick the schedule by timing candidates on the first solve
   int32_t tuned = 0;
   TileSet tiles;
   SellData sell_a;           // A in SELL-32 (pattern and float64 / float32 values)
   DevMem sell_v64, sell_v32;
+  SellData bsell_a;          // A in the 3 x 3 block layout (when it is made of dense 3 x 3 blocks)
+  DevMem bsell_v64, bsell_v32;
 };
 
 }  // namespace spai
@@ -148,8 +154,13 @@ int build_sell(const int32_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int
 // values of a CSR (dtype dt_in) into the SELL-32 layout (dtype dt_out)
 int sell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val, int dt_in, void* out, int dt_out,
                 cudaStream_t s);
-// G and G^T values of a preconditioner in its pattern's SELL-32 layout
+// G and G^T values of a preconditioner in its pattern's SELL-32 and 3 x 3 block layouts
 int precond_sell(PrecondData& M, cudaStream_t s);
+// 3 x 3 block layout of a CSR made of dense 3 x 3 blocks (out.nslices stays 0 otherwise)
+int build_bsell(const int32_t* rp, const int32_t* ci, int64_t n, int64_t nnz, SellData& out, cudaStream_t s);
+// values of such a CSR (dtype dt_in) into the block layout (dtype dt_out, 9 per block)
+int bsell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val, int dt_in, void* out, int dt_out,
+                 cudaStream_t s);
 // ||A|| = mean |A_ij| (Sec. 3.3) into out[0] (device), deterministic
 int matrix_abs_mean(const double* val, int64_t nnz, double* out, cudaStream_t s);
 int num_sms();

@@ -445,10 +445,22 @@ int sell_values(const SellData& L, const int32_t* rp, int64_t n, const void* val
 
 int precond_sell(PrecondData& M, cudaStream_t s) {
   const PatternData& P = *M.P;
-  if (P.kind != SPAI_PATTERN_FULL || P.sell.nslices <= 0) return SPAI_OK;
+  if (P.kind != SPAI_PATTERN_FULL) return SPAI_OK;
   const size_t gs = dtype_size(M.gtype);
-  const size_t bytes = (size_t)(P.sell.total + 64) * gs;
   int rc;
+  if (P.bsell.nslices > 0) {
+    const size_t bb = (size_t)(9 * P.bsell.total + 64) * gs;
+    if ((rc = M.bsell_g.alloc(bb, s))) return rc;
+    if ((rc = M.bsell_gt.alloc(bb, s))) return rc;
+    SPAI_CUDA(cudaMemsetAsync(M.bsell_g.p, 0, bb, s));
+    SPAI_CUDA(cudaMemsetAsync(M.bsell_gt.p, 0, bb, s));
+    if ((rc = bsell_values(P.bsell, P.g_rp(), P.n, M.g_val.p, M.gtype, M.bsell_g.p, M.gtype, s))) return rc;
+    if ((rc = bsell_values(P.bsell, P.gt_rp(), P.n, M.gt_val.p, M.gtype, M.bsell_gt.p, M.gtype, s))) return rc;
+    M.bsell_g.keep();
+    M.bsell_gt.keep();
+  }
+  if (P.sell.nslices <= 0) return SPAI_OK;
+  const size_t bytes = (size_t)(P.sell.total + 64) * gs;
   if ((rc = M.sell_g.alloc(bytes, s))) return rc;
   if ((rc = M.sell_gt.alloc(bytes, s))) return rc;
   SPAI_CUDA(cudaMemsetAsync(M.sell_g.p, 0, bytes, s));
@@ -497,6 +509,7 @@ extern "C" int spai_build_pattern(const spai_csr* A, int32_t kind, spai_pattern*
                                                      P->perm.as<int32_t>(), flags.as<int>()); count_launch();
     SPAI_CUDA(cudaGetLastError());
     if ((rc = build_sell(P->g_rp(), P->g_ci(), n, A->nnz, max_row, P->sell, s))) return rc;
+    if ((rc = build_bsell(P->g_rp(), P->g_ci(), n, A->nnz, P->bsell, s))) return rc;
   } else {
     const int lower_g = (kind == SPAI_PATTERN_LOWER) ? 1 : 0;
     DevMem cnt;

@@ -59,7 +59,7 @@ class _Res(C.Structure):
 
 class _Sched(C.Structure):
     _fields_ = [("tile_nnz", C.c_int32), ("items_log2", C.c_int32), ("staged", C.c_int32), ("sell", C.c_int32),
-                ("fuse", C.c_int32), ("tuned", C.c_int32)]
+                ("fuse", C.c_int32), ("block", C.c_int32), ("tuned", C.c_int32)]
 
 
 class _AdamW(C.Structure):
@@ -69,7 +69,8 @@ class _AdamW(C.Structure):
 
 class _Layout(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int32), ("sell_slices", C.c_int32),
-                ("sell_total", C.c_int64), ("sell_sorted", C.c_int32), ("pad", C.c_int32)]
+                ("sell_total", C.c_int64), ("sell_sorted", C.c_int32), ("block_slices", C.c_int32),
+                ("block_total", C.c_int64)]
 
 
 class _ServeCfg(C.Structure):
@@ -280,10 +281,10 @@ class System(_Handle):
     def layout(self):
         lo = _Layout()
         _check(lib().spai_system_info(self.h, C.byref(lo)))
-        return {k: getattr(lo, k) for k, _ in _Layout._fields_ if k != "pad"}
+        return {k: getattr(lo, k) for k, _ in _Layout._fields_}
 
-    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1, fuse=1):
-        sc = _Sched(tile_nnz, items_log2, staged, sell, fuse, 0)
+    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1, fuse=1, block=1):
+        sc = _Sched(tile_nnz, items_log2, staged, sell, fuse, block, 0)
         _check(lib().spai_system_set_schedule(self.h, C.byref(sc)))
 
 

@@ -468,3 +468,82 @@ def test_fused_step_is_bit_identical(spai_lib, case):
         assert torch.equal(a, b)
     for a, b in zip(h0, h1):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_block_layout_matches_oracle(spai_lib, mixed):
+    # a matrix made of dense 3 x 3 blocks (Sec. 3.2.2, b = 3) read in the
+    # block layout: one column index per block, a lane per block row.
+    # float64 with G = D^-1/2 on A's pattern: every ||r_k|| as the oracle's;
+    # mixed with the block GNN's G: the float64 rtol, about the float64
+    # iteration count, and the scalar layout's iteration count
+    spai = spai_lib
+    A, feat = W.elastic3d(7)
+    dA = upload(spai, A)
+    S = spai.system_create(dA)
+    lay = S.layout()
+    assert lay["block_slices"] == (A.n // 3 + 31) // 32 and lay["block_total"] * 9 >= A.nnz
+    b = W.rhs_uniform(A.n, 61)
+    pat = spai.build_pattern(dA, spai.PATTERN_FULL)
+    if not mixed:
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        diag = A.val[A.colidx == rows]
+        g = np.where(A.colidx == rows, 1.0 / np.sqrt(diag[rows]), 0.0)
+        M = spai.precond_from_values(pat, torch.tensor(g, device="cuda"), spai.F64, eps=0.0)
+        ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, A.rowptr, A.colidx, g, 0.0), rtol=1e-9)
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        h = torch.zeros(20000, dtype=torch.float64, device="cuda")
+        r = spai.system_solve(S, M, torch.tensor(b, device="cuda"), x, history=h, rtol=1e-9)
+        assert S.schedule()["block"] == 1
+        assert r["status"] == 0 and r["iters"] == ref.iters
+        k = r["history_written"]
+        assert_history_parity(h[:k].cpu().numpy(), ref.history, np.linalg.norm(b))
+        assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+        return
+    blob = W.gnn_random_weights(feat.shape[1], 4, b=3)
+    M = spai.gnn_precond(dA, pat, torch.tensor(feat.astype(np.float32), device="cuda"),
+                         torch.tensor(blob, device="cuda"), d_node=feat.shape[1], g_dtype=spai.F32, eps=0.3, block=3)
+    its = {}
+    for blk in (1, 0):
+        S.set_schedule(block=blk)
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        r = spai.system_solve(S, M, torch.tensor(b, device="cuda"), x, precision=spai.PREC_MIXED)
+        assert r["status"] == 0
+        assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x.cpu().numpy(), b) <= 1e-8
+        its[blk] = r["iters"]
+    assert abs(its[1] - its[0]) <= 0.05 * its[0] + 2, its
+
+
+def test_block_layout_alone_equals_batch(spai_lib):
+    # the block member of a batch (run by the full kernel with a SELL-32 and
+    # a CSR member) gives bit-identical results to its solve alone
+    spai = spai_lib
+    A, feat = W.elastic3d(6)
+    dA = upload(spai, A)
+    S = spai.system_create(dA)
+    pat = spai.build_pattern(dA, spai.PATTERN_FULL)
+    M = spai.gnn_precond(dA, pat, torch.tensor(feat.astype(np.float32), device="cuda"),
+                         torch.tensor(W.gnn_random_weights(feat.shape[1], 4, b=3), device="cuda"),
+                         d_node=feat.shape[1], g_dtype=spai.F32, eps=0.3, block=3)
+    b = torch.tensor(W.rhs_uniform(A.n, 62), device="cuda")
+    x1 = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r1 = spai.system_solve(S, M, b, x1, precision=spai.PREC_MIXED)
+    B = W.aniso2d(50, 10.0, 0.4)
+    dB = upload(spai, B)
+    SB = spai.system_create(dB)
+    pB = spai.build_pattern(dB, spai.PATTERN_FULL)
+    MB = spai.gnn_precond(dB, pB, torch.tensor(W.row_average_feature(B), device="cuda"),
+                          torch.tensor(W.gnn_random_weights(1, 4), device="cuda"), d_node=1, g_dtype=spai.F32, eps=0.3)
+    C = W.graph_laplacian(800, 6400, seed=3)
+    dC = upload(spai, C)
+    SC = spai.system_create(dC)
+    SC.set_schedule(sell=0)
+    pC = spai.build_pattern(dC, spai.PATTERN_FULL)
+    MC = spai.gnn_precond(dC, pC, torch.tensor(W.row_average_feature(C), device="cuda"),
+                          torch.tensor(W.gnn_random_weights(1, 4), device="cuda"), d_node=1, g_dtype=spai.F32, eps=0.3)
+    bs = [b, torch.tensor(W.rhs_uniform(B.n, 63), device="cuda"), torch.tensor(W.rhs_uniform(C.n, 64), device="cuda")]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device="cuda"), torch.zeros(B.n, dtype=torch.float64, device="cuda"),
+          torch.zeros(C.n, dtype=torch.float64, device="cuda")]
+    res = spai.pcg_solve_batched([S, SB, SC], [M, MB, MC], bs, xs, precision=spai.PREC_MIXED)
+    assert all(r["status"] == 0 for r in res)
+    assert res[0]["iters"] == r1["iters"] and torch.equal(xs[0], x1)
