@@ -718,7 +718,9 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   const int32_t* tl = S.tiles[m];
   const bool piped = S.fits[m] != 0;
   const int32_t* sp = S.fmt[m] == 1 ? S.sptr[m] : nullptr;  // SELL-32 slices
-  const int32_t* srow = S.fmt[m] == 1 ? S.srow[m] : nullptr;  // their rows, when sorted by length
+  // their rows when sorted by length: a row map only the full kernel reads
+  // (launches with such a member run it), so the SELL-32 kernel's loop stays as it was
+  const int32_t* srow = (CSR && S.fmt[m] == 1) ? S.srow[m] : nullptr;
   const int64_t n = S.n;
   const int rpu = rows_per_unit(S.fmt[m]);
   // 3 x 3 block layout: compiled into the full kernel only (launches with a
@@ -1421,7 +1423,7 @@ class EngineBatch {
       for (int mm = 0; mm < 3; ++mm) {
         e.fits[mm] = e.fmt[mm] ? 1 : fits;
         if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
-        if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2) csr_ring = true;  // the full kernel
+        if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2 || e.srow[mm]) csr_ring = true;  // the full kernel
       }
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
