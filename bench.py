@@ -1145,9 +1145,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     # DRAM bytes per inner iteration of the current persistent kernel at 128^3 from its ncu capture
-    # (profiles/engine_kernel_diffusion3d_128.md: 12.30 GB for 30 iterations plus the float64 start and
+    # (profiles/engine_kernel_diffusion3d_128.md: 12.40 GB for 30 iterations plus the float64 start and
     # one refinement, about 0.85 GB); 0 reports null
-    ap.add_argument("--traffic-per-iter", type=float, default=3.82e8,
+    ap.add_argument("--traffic-per-iter", type=float, default=3.85e8,
                     help="DRAM bytes per inner iteration from an ncu capture of the current kernel")
     ap.add_argument("--workload", default="diffusion3d",
                     choices=["diffusion3d", "graph", "batch", "serve", "ppt", "fsai", "trained", "elastic"])

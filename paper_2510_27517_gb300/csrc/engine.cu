@@ -697,9 +697,15 @@ __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* t
   }
 }
 
-template <class VT, class GT, bool MIXED, bool CSR>
+// Kernel variants: KV 0 streams SELL-32 slices in row order only, KV 1 also
+// row-mapped slices (rows sorted by length), KV 2 everything (CSR row groups
+// through the ring, the 3 x 3 block layout, row maps).  A launch runs the
+// smallest variant its members need: each extra path costs the SELL-32 loop
+// registers and time.
+template <class VT, class GT, bool MIXED, int KV>
 __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P, void* sbuf,
                          double* red, double& p0, double& p1, uint64_t limit_ns, int* err, int rc) {
+  constexpr bool CSR = KV == 2;
   const int dc = st.dc;
   VT* r_cur = reinterpret_cast<VT*>(S.r[rc]);
   VT* r_nxt = reinterpret_cast<VT*>(S.r[rc ^ 1]);
@@ -718,9 +724,9 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
   const int32_t* tl = S.tiles[m];
   const bool piped = S.fits[m] != 0;
   const int32_t* sp = S.fmt[m] == 1 ? S.sptr[m] : nullptr;  // SELL-32 slices
-  // their rows when sorted by length: a row map only the full kernel reads
-  // (launches with such a member run it), so the SELL-32 kernel's loop stays as it was
-  const int32_t* srow = (CSR && S.fmt[m] == 1) ? S.srow[m] : nullptr;
+  // their rows when sorted by length: a row map only variants 1 and 2 read,
+  // so the plain SELL-32 kernel's loop stays as it was
+  const int32_t* srow = (KV >= 1 && S.fmt[m] == 1) ? S.srow[m] : nullptr;
   const int64_t n = S.n;
   const int rpu = rows_per_unit(S.fmt[m]);
   // 3 x 3 block layout: compiled into the full kernel only (launches with a
@@ -957,7 +963,7 @@ __device__ __forceinline__ void load_state(const EngState* src, EngState* dst) {
   for (int i = 0; i < (int)(sizeof(EngState) / 8); ++i) d[i] = __ldcg(s + i);
 }
 
-template <class VT, class GT, bool MIXED, bool CSR>
+template <class VT, class GT, bool MIXED, int KV>
 __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   using MVmax = typename std::conditional<MIXED, float, double>::type;
   __shared__ double red[64];
@@ -1011,7 +1017,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
         // the G pass of a fused step reads r' = r - alpha q, which the G^T pass wrote to r[rc ^ 1]
         const int rc = pass == 1 ? (s_st.rc ^ 1) : s_st.rc;
         double p0 = 0.0, p1 = 0.0;
-        if (g0 < g1) run_item<VT, GT, MIXED, CSR>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err,
+        if (g0 < g1) run_item<VT, GT, MIXED, KV>(ph, S, s_st, g0, g1, P, sbuf, red, p0, p1, a.limit_ns, &a.gs->err,
                                                   rc);
         block_sum2(p0, p1, red);
         double* pbase = a.partial + 2 * (size_t)S.item_base;
@@ -1191,20 +1197,21 @@ __global__ void engine_continue_kernel(GridSync* gs, int64_t slot_cap, cudaGraph
 }
 
 template <class VT, class GT, bool MIXED>
-const void* kernel_ptr(bool csr) {
-  return csr ? reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, true>)
-             : reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, false>);
+const void* kernel_ptr(int kv) {
+  if (kv == 0) return reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, 0>);
+  if (kv == 1) return reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, 1>);
+  return reinterpret_cast<const void*>(&engine_kernel<VT, GT, MIXED, 2>);
 }
 
-const void* select_kernel(bool mixed, int gtype, bool csr) {
+const void* select_kernel(bool mixed, int gtype, int kv) {
   if (!mixed) {
-    if (gtype == SPAI_F64) return kernel_ptr<double, double, false>(csr);
-    if (gtype == SPAI_F32) return kernel_ptr<double, float, false>(csr);
+    if (gtype == SPAI_F64) return kernel_ptr<double, double, false>(kv);
+    if (gtype == SPAI_F32) return kernel_ptr<double, float, false>(kv);
     return nullptr;
   }
-  if (gtype == SPAI_F32) return kernel_ptr<float, float, true>(csr);
-  if (gtype == SPAI_BF16) return kernel_ptr<float, __nv_bfloat16, true>(csr);
-  if (gtype == SPAI_F16) return kernel_ptr<float, __half, true>(csr);
+  if (gtype == SPAI_F32) return kernel_ptr<float, float, true>(kv);
+  if (gtype == SPAI_BF16) return kernel_ptr<float, __nv_bfloat16, true>(kv);
+  if (gtype == SPAI_F16) return kernel_ptr<float, __half, true>(kv);
   return nullptr;
 }
 
@@ -1304,8 +1311,9 @@ class EngineBatch {
     mixed_ = mixed;
     s_ = s;
     opts_ = o;
-    kfn_csr_ = select_kernel(mixed, gtype, true);
-    kfn_sell_ = select_kernel(mixed, gtype, false);
+    for (int kv = 0; kv < 3; ++kv) kfns_[kv] = select_kernel(mixed, gtype, kv);
+    kfn_csr_ = kfns_[2];
+    kfn_sell_ = kfns_[0];
     kfn_ = kfn_csr_;
     if (!kfn_)
       return set_error(SPAI_ERR_INVALID, mixed ? "mixed precision needs G stored as F32, BF16 or F16"
@@ -1313,11 +1321,12 @@ class EngineBatch {
     smem_max_ = engine_smem_bytes(mixed);
     smem_ = smem_max_;
     int per_sell = 0;
-    SPAI_CUDA(cudaFuncSetAttribute(kfn_csr_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
-    SPAI_CUDA(cudaFuncSetAttribute(kfn_sell_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
-    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_, kfn_csr_, kBlock, smem_max_));
-    SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sell, kfn_sell_, kBlock, smem_max_));
-    if (per_sell < per_sm_) per_sm_ = per_sell;  // one grid for both kernels
+    per_sm_ = 1 << 30;
+    for (int kv = 0; kv < 3; ++kv) {
+      SPAI_CUDA(cudaFuncSetAttribute(kfns_[kv], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_));
+      SPAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sell, kfns_[kv], kBlock, smem_max_));
+      if (per_sell < per_sm_) per_sm_ = per_sell;  // one grid for every variant
+    }
     if (per_sm_ < 1) return set_error(SPAI_ERR_CUDA, "engine kernel cannot be resident");
     grid_max_ = per_sm_ * num_sms();
     return SPAI_OK;
@@ -1334,7 +1343,8 @@ class EngineBatch {
     std::vector<EngSys> hs(nsys);
     int64_t items = 0, chunks = 0, nmax = 0;
     int live = 0;
-    bool csr_ring = false;  // a member streams CSR groups through the ring
+    bool csr_ring = false;  // a member streams CSR groups through the ring (or uses the block layout)
+    bool rmap = false;      // a member has row-mapped SELL-32 slices
     for (int i = 0; i < nsys; ++i) {
       const Member& mb = members[i];
       SystemData& A = *mb.S;
@@ -1423,7 +1433,8 @@ class EngineBatch {
       for (int mm = 0; mm < 3; ++mm) {
         e.fits[mm] = e.fmt[mm] ? 1 : fits;
         if (e.ntiles[mm] > ng) ng = e.ntiles[mm];
-        if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2 || e.srow[mm]) csr_ring = true;  // the full kernel
+        if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2) csr_ring = true;  // the full kernel
+        if (e.srow[mm]) rmap = true;
       }
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
@@ -1455,7 +1466,7 @@ class EngineBatch {
     }
     if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
     smem_ = engine_smem_bytes(mixed_, csr_ring);
-    kfn_ = csr_ring ? kfn_csr_ : kfn_sell_;
+    kfn_ = kfns_[csr_ring ? 2 : (rmap ? 1 : 0)];
     std::vector<int32_t> isys(items), itile(items);
     for (int i = 0; i < nsys; ++i)
       for (int v = 0; v < hs[i].nitems; ++v) {
@@ -1657,7 +1668,8 @@ class EngineBatch {
   bool mixed_ = false;
   cudaStream_t s_ = nullptr;
   spai_pcg_opts opts_;
-  const void* kfn_ = nullptr;  // this launch's kernel: kfn_csr_ or kfn_sell_
+  const void* kfns_[3] = {nullptr, nullptr, nullptr};  // kernel variants 0, 1, 2
+  const void* kfn_ = nullptr;  // this launch's kernel
   const void* kfn_csr_ = nullptr;
   const void* kfn_sell_ = nullptr;
   size_t smem_ = 0, smem_max_ = 0;  // this launch's dynamic shared memory; the largest
@@ -2042,7 +2054,7 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
   const int64_t n = A->n;
 
   // kernel and grid
-  const void* kfn = select_kernel(false, SPAI_F64, true);
+  const void* kfn = select_kernel(false, SPAI_F64, 2);
   const int block = kBlock;
   const size_t smem = engine_smem_bytes(false);
   SPAI_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
