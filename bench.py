@@ -608,7 +608,10 @@ def run_batch(args):
         A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
         P, M = _gnn_for(spai, A, A_h, W.row_average_feature(A_h).astype(np.float32), blob, 1, spai.F32, args.eps)
         S = spai.system_create(A, autotune=args.autotune)
-        systems.append(S), preconds.append(M), keep.append((A, P))
+        S1 = spai.system_create(A, autotune=args.autotune)  # one-at-a-time: the schedule for a solve alone
+        if args.batch_items_log2:
+            S.set_schedule(items_log2=args.batch_items_log2)
+        systems.append(S), preconds.append(M), keep.append((A, P, S1))
         bs.append(torch.tensor(W.rhs_uniform(A_h.n, W.BASE_SEED + 1000 + i), device="cuda"))
         sum_n += A_h.n
         sum_nnz += A_h.nnz
@@ -646,10 +649,11 @@ def run_batch(args):
     if not args.no_alone:
         def seq():
             out = []
-            for S, M, b, x in zip(systems, preconds, bs, xs):
+            for (_, _, S1), M, b, x in zip(keep, preconds, bs, xs):
                 x.zero_()
-                out.append(spai.system_solve(S, M, b, x, **kw))
+                out.append(spai.system_solve(S1, M, b, x, **kw))
             return out
+        seq()
         _, alone_ms = _timed(seq)
     peak, src = _peak_hbm()
     iters = [r["iters"] for r in res]
@@ -657,7 +661,10 @@ def run_batch(args):
                         "solves/s",
                         {"workload": f"{args.batch} anisotropic 2D systems, sides log-uniform [32, {args.batch_side_hi}], "
                                      f"GNN-SPAI G (f32), eps {args.eps}, f32 PCG in f64 refinement",
-                         "sum_n": sum_n, "sum_nnz": sum_nnz, "autotune": bool(args.autotune)},
+                         "sum_n": sum_n, "sum_nnz": sum_nnz, "autotune": bool(args.autotune),
+                         "batch_schedule": f"items_log2 {args.batch_items_log2} (groups per work item x "
+                                           f"2^{args.batch_items_log2} of a solve alone); one-at-a-time: "
+                                           f"the default schedule"},
                         {"ms_per_batch": ms, "engine_ms": eng_ms, "iters_min": min(iters), "iters_max": max(iters),
                          "iters_mean": statistics.mean(iters),
                          "aggregate": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
@@ -768,9 +775,12 @@ def run_serve(args):
             gdt_srv = spai.BF16 if args.serve_gdtype == "bf16" else spai.F32
             P32, M32 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, gdt_srv, args.eps)
             P64, M64 = _gnn_for(spai, A, A_h, feat.astype(np.float32), blob, d_node, spai.F64, args.eps)
-            S = spai.system_create(A)
-            pool.append({"gen": gen, "n": A_h.n, "nnz": A_h.nnz, "A": A, "S": S, "M32": M32, "M64": M64,
-                         "keep": (P32, P64)})
+            S = spai.system_create(A)          # float64 one-at-a-time: the schedule for a solve alone
+            S_srv = spai.system_create(A)      # served: larger work items (many systems share a launch)
+            if args.batch_items_log2:
+                S_srv.set_schedule(items_log2=args.batch_items_log2)
+            pool.append({"gen": gen, "n": A_h.n, "nnz": A_h.nnz, "A": A, "S": S, "S_srv": S_srv, "M32": M32,
+                         "M64": M64, "keep": (P32, P64)})
     R = args.requests
     sys_of = g.integers(0, len(pool), size=R)
     b_host = [torch.from_numpy(W.rhs_uniform(pool[s]["n"], W.BASE_SEED + 10_000 + i)).pin_memory()
@@ -811,7 +821,7 @@ def run_serve(args):
 
     srv = spai.Server(hbm_cap_bytes=args.hbm_cap_gb << 30, max_slots=args.max_slots, chunk_iters=args.chunk_iters,
                       precision=spai.PREC_MIXED, rtol=1e-8, max_iter=args.max_iter)
-    ids = [srv.register(p["S"], p["M32"]) for p in pool]
+    ids = [srv.register(p["S_srv"], p["M32"]) for p in pool]
     # warm the server
     for i in range(min(3, R)):
         srv.wait(srv.submit(ids[sys_of[i]], b_host[i], x_host[i]), timeout_ms=600000)
@@ -850,7 +860,7 @@ def run_serve(args):
                         {"workload": f"{R} requests over 48 systems (Poisson 2D, diffusion 3D, graph Laplacian), "
                                      f"n log-uniform [{args.serve_n_lo}, {args.serve_n_hi}], Poisson arrivals",
                          "hbm_cap_gb": args.hbm_cap_gb, "max_slots": args.max_slots, "chunk_iters": args.chunk_iters,
-                         "served_g_dtype": args.serve_gdtype,
+                         "served_g_dtype": args.serve_gdtype, "served_items_log2": args.batch_items_log2,
                          "eps": args.eps},
                         {"mu64_solves_per_s": mu64, "ratio_vs_f64_one_at_a_time": top["served"]["solves_per_s"] / mu64,
                          "rates": rates, "clocks": clk,
@@ -1162,6 +1172,8 @@ def main():
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-side-hi", type=int, default=512)
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--batch-items-log2", type=int, default=4,
+                    help="batch and served systems: groups per work item x 2^this (-4..4) of a solve alone")
     ap.add_argument("--no-alone", action="store_true")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rates", default="0.5,1,2,4,8")

@@ -547,3 +547,32 @@ def test_block_layout_alone_equals_batch(spai_lib):
     res = spai.pcg_solve_batched([S, SB, SC], [M, MB, MC], bs, xs, precision=spai.PREC_MIXED)
     assert all(r["status"] == 0 for r in res)
     assert res[0]["iters"] == r1["iters"] and torch.equal(xs[0], x1)
+
+
+@pytest.mark.parametrize("side", [12, 16])
+def test_trained_gnn_every_iteration_matches_oracle(spai_lib, side):
+    # with the trained weights the float64 iteration is not chaotic (unlike a
+    # random-weight G): every ||r_k|| agrees with the oracle's Algorithm 1 at
+    # the 1e-10 bar, the iteration counts are equal and x agrees to 1e-8
+    import os
+    spai = spai_lib
+    wpath = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2510_27517_gb300",
+                         "weights", "gnn_diffusion3d_l4.npy")
+    blob = np.load(wpath).astype(np.float32)
+    A, k = W.diffusion3d(side, seed=W.BASE_SEED + 77)
+    v = W.diffusion3d_node_features(k)
+    dA = upload(spai, A)
+    P = spai.build_pattern(dA, spai.PATTERN_FULL)
+    M = spai.gnn_precond(dA, P, torch.tensor(v, device="cuda"), torch.tensor(blob, device="cuda"), d_node=4,
+                         g_dtype=spai.F64, eps=1e-4)
+    g, _ = M.export(spai.F64)
+    b = W.rhs_uniform(A.n, 81)
+    ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, A.rowptr, A.colidx, g.cpu().numpy(), 1e-4),
+                  rtol=1e-8)
+    res, x, hist = gpu_solve(spai, dA, M, b, hist_len=4096)
+    assert res["status"] == 0 and ref.status == pcg.CONVERGED
+    assert res["iters"] == ref.iters and ref.iters < 200
+    k_ = res["history_written"]
+    assert k_ == len(ref.history)
+    assert_history_parity(hist[:k_], ref.history, np.linalg.norm(b))
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
