@@ -55,7 +55,12 @@ def make_host_workload(args, rank: int, grid: int = 0, weights: str = "random"):
 
     A, k = W.diffusion3d(grid or args.grid, 1.5, 8.0, seed=W.BASE_SEED + 2)
     v = W.diffusion3d_node_features(k)
-    blob = trained_blob() if weights == "trained" else W.gnn_random_weights(4, 4, seed=W.BASE_SEED + 100)
+    if weights == "trained":
+        blob = trained_blob()
+        if trained_meta().get("features") == "logk":  # the trained GNN reads the log coefficient alone
+            v = np.ascontiguousarray(v[:, 3:4])
+    else:
+        blob = W.gnn_random_weights(4, 4, seed=W.BASE_SEED + 100)
     b = W.rhs_uniform(A.n, W.BASE_SEED + 10 + rank)
     return {"A": A, "v": v, "blob": blob, "b": b.astype(np.float64)}
 
@@ -67,6 +72,10 @@ def trained_blob():
     """The GNN weights trained on the SAI loss (paper_2510_27517_gb300/train.py)."""
     import numpy as np
     return np.load(TRAINED + ".npy").astype(np.float32)
+
+
+def trained_meta():
+    return json.load(open(TRAINED + ".json"))
 
 
 def algorithmic_bytes(n, nnz_a, nnz_g, s_v, s_g):
@@ -952,7 +961,7 @@ def run_trained(args):
                             ("f64", spai.PREC_F64, spai.F64)):
         def step():
             P = spai.build_pattern(A, spai.PATTERN_FULL)
-            M = spai.gnn_precond(A, P, v, w, d_node=4, n_layers=4, g_dtype=gdt, eps=eps)
+            M = spai.gnn_precond(A, P, v, w, d_node=v.shape[1], n_layers=4, g_dtype=gdt, eps=eps)
             x.zero_()
             r = spai.pcg_solve(A, M, b, x, precision=prec, rtol=1e-8, max_iter=args.max_iter)
             M.close(), P.close()

@@ -44,11 +44,20 @@ if ROOT not in sys.path:
 import paper_2510_27517_gb300 as spai  # noqa: E402
 import workloads as W  # noqa: E402
 
-D_NODE = 4
+D_NODE = 4  # node feature width; 1 with --features logk
 LAYERS = 4
 
 
-def dataset(count: int, sides, seed0: int, sigmas=(1.5,)):
+def node_features(k, features="pos_logk"):
+    """Node features of a diffusion matrix: cell position in [-1, 1]^3 and
+    log coefficient (d_node 4), or the log coefficient alone (d_node 1: the
+    field is stationary, so position says nothing about the operator, and
+    it means a different distance to the boundary on every grid size)."""
+    f = W.diffusion3d_node_features(k)
+    return np.ascontiguousarray(f[:, 3:4]) if features == "logk" else f
+
+
+def dataset(count: int, sides, seed0: int, sigmas=(1.5,), features="pos_logk"):
     """`count` diffusion matrices, grid sides cycling through `sides` and
     field contrasts through `sigmas` (k = exp(sigma g)), each with its own
     random-field seed."""
@@ -57,7 +66,7 @@ def dataset(count: int, sides, seed0: int, sigmas=(1.5,)):
         N = sides[i % len(sides)]
         sg = sigmas[(i // len(sides)) % len(sigmas)]
         A, k = W.diffusion3d(N, sg, 8.0, seed=seed0 + i)
-        out.append({"N": N, "sigma": sg, "seed": seed0 + i, "A_h": A, "feat": W.diffusion3d_node_features(k)})
+        out.append({"N": N, "sigma": sg, "seed": seed0 + i, "A_h": A, "feat": node_features(k, features)})
     return out
 
 
@@ -127,6 +136,8 @@ def main():
     ap.add_argument("--weight-decay", type=float, default=0.01)
     ap.add_argument("--clip", type=float, default=1.0, help="gradient 2-norm bound (0: none)")
     ap.add_argument("--eps", type=float, default=1e-4, help="shift of M^-1 = G G^T + eps I in training (the text's 1e-4)")
+    ap.add_argument("--features", default="pos_logk", choices=["pos_logk", "logk"],
+                    help="node features: position + log coefficient (d_node 4) or log coefficient alone (d_node 1)")
     ap.add_argument("--seed", type=int, default=W.BASE_SEED + 500)
     ap.add_argument("--eval-eps", type=float, default=1e-2, help="also evaluate with this shift")
     ap.add_argument("--eval-sides", default="48,64",
@@ -135,15 +146,18 @@ def main():
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2510_27517_gb300", "weights", "gnn_diffusion3d_l4"))
     args = ap.parse_args()
 
+    global D_NODE
+    D_NODE = 1 if args.features == "logk" else 4
     torch.cuda.set_device(0)
     spai.lib()
     sides = [int(s) for s in args.sides.split(",")]
     sigmas = [float(s) for s in args.sigmas.split(",")]
-    data = [to_device(it) for it in dataset(args.matrices, sides, args.seed, sigmas)]
+    data = [to_device(it) for it in dataset(args.matrices, sides, args.seed, sigmas, args.features)]
     n_test = max(1, args.matrices // 5)
     train, test = data[:-n_test], data[-n_test:]
 
     init = W.gnn_random_weights(D_NODE, LAYERS, seed=W.BASE_SEED + 100)
+    init_desc = f"workloads.gnn_random_weights({D_NODE}, {LAYERS}, seed=BASE_SEED + 100)"
     blob = torch.tensor(init, device="cuda")
     master = blob.to(torch.float64).clone()
     m = torch.zeros_like(master)
@@ -184,12 +198,12 @@ def main():
     init_blob = torch.tensor(init, device="cuda")
     extra = []
     for j, side in enumerate(int(x) for x in args.eval_sides.split(",") if x):
-        extra += [to_device(it) for it in dataset(1, [side], args.seed + 10_000 + j)]
+        extra += [to_device(it) for it in dataset(1, [side], args.seed + 10_000 + j, (1.5,), args.features)]
     if args.eval_bench:
         # the benchmark's own matrix (diffusion 128^3, sigma 1.5, its seed): evaluated, never trained on
         A, k = W.diffusion3d(128, 1.5, 8.0, seed=W.BASE_SEED + 2)
         extra.append(to_device({"N": 128, "sigma": 1.5, "seed": W.BASE_SEED + 2, "A_h": A,
-                                "feat": W.diffusion3d_node_features(k)}))
+                                "feat": node_features(k, args.features)}))
     for it in test + extra:
         evals.append({"N": it["N"], "sigma": it["sigma"], "seed": it["seed"], "n": it["A_h"].n,
                       "trained": pcg_iters(it, blob, args.eps, "gnn"),
@@ -210,7 +224,7 @@ def main():
             "optimiser": {"kind": "AdamW", "lr": args.lr, "decay_per_epoch": args.decay,
                           "weight_decay": args.weight_decay, "clip": args.clip, "batch": args.batch,
                           "probes": args.probes, "epochs": args.epochs, "steps": step},
-            "init": "workloads.gnn_random_weights(4, 4, seed=BASE_SEED + 100)",
+            "init": init_desc, "features": args.features,
             "test_loss_init": test_loss0, "test_loss_final": curve[-1].get("test_loss"),
             "train_seconds": train_s, "curve": [c for c in curve if "test_loss" in c],
             "eval_pcg_f64_rtol1e-8": evals,

@@ -554,17 +554,21 @@ def test_trained_gnn_every_iteration_matches_oracle(spai_lib, side):
     # with the trained weights the float64 iteration is not chaotic (unlike a
     # random-weight G): every ||r_k|| agrees with the oracle's Algorithm 1 at
     # the 1e-10 bar, the iteration counts are equal and x agrees to 1e-8
+    import json
     import os
     spai = spai_lib
-    wpath = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2510_27517_gb300",
-                         "weights", "gnn_diffusion3d_l4.npy")
-    blob = np.load(wpath).astype(np.float32)
+    wbase = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2510_27517_gb300",
+                         "weights", "gnn_diffusion3d_l4")
+    blob = np.load(wbase + ".npy").astype(np.float32)
+    meta = json.load(open(wbase + ".json"))
     A, k = W.diffusion3d(side, seed=W.BASE_SEED + 77)
     v = W.diffusion3d_node_features(k)
+    if meta.get("features") == "logk":
+        v = np.ascontiguousarray(v[:, 3:4])
     dA = upload(spai, A)
     P = spai.build_pattern(dA, spai.PATTERN_FULL)
-    M = spai.gnn_precond(dA, P, torch.tensor(v, device="cuda"), torch.tensor(blob, device="cuda"), d_node=4,
-                         g_dtype=spai.F64, eps=1e-4)
+    M = spai.gnn_precond(dA, P, torch.tensor(v, device="cuda"), torch.tensor(blob, device="cuda"),
+                         d_node=v.shape[1], g_dtype=spai.F64, eps=1e-4)
     g, _ = M.export(spai.F64)
     b = W.rhs_uniform(A.n, 81)
     ref = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, pcg.spai_apply(A.n, A.rowptr, A.colidx, g.cpu().numpy(), 1e-4),
