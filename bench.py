@@ -1091,6 +1091,15 @@ def run_probe(args):
     P = spai.build_pattern(A, spai.PATTERN_FULL)
     M = spai.gnn_precond(A, P, torch.tensor(h["v"], device="cuda"), torch.tensor(h["blob"], device="cuda"), d_node=4,
                          n_layers=4, g_dtype=spai.F32, eps=args.eps)
+    # GNN forward (pattern given), median of 5
+    gnn_ms = []
+    for _ in range(5):
+        def fwd():
+            return spai.gnn_precond(A, P, torch.tensor(h["v"], device="cuda"), torch.tensor(h["blob"], device="cuda"),
+                                    d_node=4, n_layers=4, g_dtype=spai.F32, eps=args.eps)
+        M2, ms = _timed(fwd)
+        M2.close()
+        gnn_ms.append(ms)
     x = torch.zeros(A_h.n, dtype=torch.float64, device="cuda")
     S = spai.system_create(A)
     S.set_schedule(fuse=args.probe_fuse, items_log2=args.probe_klog)
@@ -1104,7 +1113,8 @@ def run_probe(args):
     torch.cuda.synchronize()
     print(json.dumps({"probe": True, "n": A_h.n, "nnz": A_h.nnz, "iters": r["iters"], "engine_ms": r["engine_ms"],
                       "ms_per_iter": r["engine_ms"] / max(1, r["iters"]), "slots": r["slots"],
-                      "fuse": args.probe_fuse, "items_log2": args.probe_klog, "precision": args.precision}))
+                      "fuse": args.probe_fuse, "items_log2": args.probe_klog, "precision": args.precision,
+                      "gnn_forward_ms": statistics.median(gnn_ms)}))
 
 
 # ---------------------------------------------------------------------------

@@ -249,15 +249,17 @@ __global__ void __launch_bounds__(ECAP) edge_kernel(const EdgeArgs a, const __gr
         if (MSG) {
           __syncthreads();
           if (!longrow) {
-            for (int row = r + threadIdx.x; row < re; row += blockDim.x) {
+            // every (row, channel) sum over the row's edges in edge order, the
+            // pairs spread over all threads (channel-major: neighbouring threads
+            // take neighbouring rows, whose edges sit in different banks)
+            const int nrows = re - r;
+            for (int p = threadIdx.x; p < nrows * H; p += blockDim.x) {
+              const int c = p / nrows;
+              const int row = r + (p - c * nrows);
               const int ea = __ldg(a.rp + row) - cb, eb = __ldg(a.rp + row + 1) - cb;
-              float* out = a.S + (int64_t)row * H;
-#pragma unroll 4
-              for (int c = 0; c < H; ++c) {
-                float s = 0.f;
-                for (int q = ea; q < eb; ++q) s += zbuf[c][q];
-                out[c] = s;
-              }
+              float s = 0.f;
+              for (int q = ea; q < eb; ++q) s += zbuf[c][q];
+              a.S[(int64_t)row * H + c] = s;
             }
           } else if (threadIdx.x < H) {
             float s = racc[threadIdx.x];
