@@ -65,3 +65,40 @@ def test_replica_aggregate_is_whole_job_throughput():
     agg = b.aggregate([2000.0, 2500.0, 1800.0], steps=5, world=3)
     assert agg["value"] == pytest.approx(3 * 5 / 2.5)
     assert agg["ms_per_step"] == pytest.approx(500.0)
+
+
+def test_reference_iteration_model_is_a_power_law_through_oracle_counts():
+    # the reference arm's iteration count: the oracle's own counts at 12^3,
+    # 16^3, 20^3 fitted as k = c N^p; at a measured grid the fit lands near
+    # the measured count, and the stated model names the counts it used
+    import math
+    import re
+    b = _bench()
+
+    class A:
+        grid = 16
+        eps = 0.3
+    k16, desc = b.iteration_model(A)
+    counts = [int(x) for x in re.search(r"= \[([0-9, ]+)\]", desc).group(1).split(",")]
+    p = float(re.search(r"N\^([0-9.]+)", desc).group(1))
+    assert len(counts) == 3 and all(c > 0 for c in counts) and p > 0
+    assert abs(math.log(k16) - math.log(counts[1])) < 0.25
+
+
+def test_trained_weights_metadata_matches_the_blob():
+    import json
+
+    import numpy as np
+
+    import workloads as W
+    b = _bench()
+    meta = json.load(open(b.TRAINED + ".json"))
+    blob = b.trained_blob()
+    assert blob.dtype == np.float32 and blob.size == meta["count"]
+    d_node = meta["d_node"]
+    assert blob.size == W.gnn_param_count(d_node, meta["n_layers"])
+    assert np.all(np.isfinite(blob))
+    # evaluated against Jacobi and plain CG on held-out matrices
+    ev = meta["eval_pcg_f64_rtol1e-8"]
+    small = [e for e in ev if e["N"] <= 24]
+    assert small and all(e["trained"] < e["jacobi"] < e["plain_cg"] for e in small)
