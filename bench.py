@@ -559,6 +559,8 @@ def run_graph(args):
     b = torch.tensor(W.rhs_normal(A_h.n, W.BASE_SEED + 30), device="cuda")
     A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
     S = spai.system_create(A)
+    if args.pair >= 0:
+        S.set_schedule(pair=args.pair)
     forms = {}
     for name, prec, gdt in (("mixed", spai.PREC_MIXED, spai.F32), ("f64", spai.PREC_F64, spai.F64)):
         P, M = _gnn_for(spai, A, A_h, feat, blob, 1, gdt, args.eps)
@@ -587,7 +589,8 @@ def run_graph(args):
         f["engine_frac_of_" + src] = f["engine_gbs"] / peak
     line = _common_line(args, "solves/s to rtol 1e-8 (graph Laplacian, mixed vs float64)",
                         1e3 / forms["mixed"]["ms_per_solve"], "solves/s",
-                        {"workload": f"graph Laplacian n={A_h.n} nnz={A_h.nnz}, GNN-SPAI G, eps {args.eps}"},
+                        {"workload": f"graph Laplacian n={A_h.n} nnz={A_h.nnz}, GNN-SPAI G, eps {args.eps}",
+                         "paired_vectors": S.schedule()["pair"]},
                         {"mixed": forms["mixed"], "f64": forms["f64"], "speedup_mixed_vs_f64":
                          forms["f64"]["ms_per_solve"] / forms["mixed"]["ms_per_solve"],
                          "rel_x_diff_mixed_vs_f64": d, "hbm_peak_gbs": peak})
@@ -1102,7 +1105,7 @@ def run_probe(args):
         gnn_ms.append(ms)
     x = torch.zeros(A_h.n, dtype=torch.float64, device="cuda")
     S = spai.system_create(A)
-    S.set_schedule(fuse=args.probe_fuse, items_log2=args.probe_klog)
+    S.set_schedule(fuse=args.probe_fuse, items_log2=args.probe_klog, pair=None if args.pair < 0 else args.pair)
     prec = spai.PREC_MIXED if args.precision == "mixed" else spai.PREC_F64
     if prec == spai.PREC_F64:
         M.close()
@@ -1188,6 +1191,8 @@ def main():
     ap.add_argument("--trained-eps", type=float, default=1e-2,
                     help="shift with the trained weights (1e-2: their best at 128^3, see weights/*.json)")
     ap.add_argument("--graph-n", type=int, default=1_000_000)
+    ap.add_argument("--pair", type=int, default=-1, choices=[-1, 0, 1],
+                    help="graph and probe: paired vectors off (0) / on (1); -1: the system's default")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-side-hi", type=int, default=512)
     ap.add_argument("--autotune", action="store_true")

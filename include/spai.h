@@ -324,6 +324,15 @@ void spai_precond_destroy(spai_precond* M);
  *               it reaches have finished (per-item flags instead of a
  *               grid-wide barrier); 0: one grid-wide step per pass.  The
  *               arithmetic is the same either way.
+ *   pair        1: the iteration vectors read at the same column in one pass
+ *               are stored as interleaved pairs (s with the search direction
+ *               d, read together by the A pass; q = A p with r, read together
+ *               by the G^T pass), so each such gather is one 8-byte (float32)
+ *               or 16-byte (float64) load instead of two loads at different
+ *               addresses; 0: separate vectors.  Default 1 for systems whose
+ *               rows were sorted by length (irregular gathers, where every
+ *               load is a separate L2 request), else 0.  The arithmetic is
+ *               the same either way.
  * Per-row sums are the same in every schedule (entries in stored order);
  * dot products are summed in a schedule-dependent fixed order.
  * The default is the heuristic schedule (sell 1).  `autotune` nonzero makes
@@ -344,6 +353,7 @@ typedef struct {
   int32_t fuse;        /* 1: G^T and G passes in one grid-wide step (default), 0: separate steps */
   int32_t block;       /* 1: the 3 x 3 block layout for A, G and G^T when they are made of dense 3 x 3
                           blocks (default), 0: scalar layouts */
+  int32_t pair;        /* 1: paired vectors (default for rows sorted by length), 0: separate vectors */
   int32_t tuned;       /* out: 1 once the autotuner ran or a schedule was set */
 } spai_schedule;
 

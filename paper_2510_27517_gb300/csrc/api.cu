@@ -252,6 +252,9 @@ int make_system(const spai_csr* A, int autotune, std::shared_ptr<SystemData>& ou
     S->sell_v64.keep();
     S->sell_v32.keep();
   }
+  // rows sorted by length mark an irregular matrix: gathers at random columns,
+  // where pairing the vectors read at the same column halves the requests
+  S->pair = S->sell_a.rows.p ? 1 : 0;
   if ((rc = build_bsell(S->rowptr.as<int32_t>(), S->colidx.as<int32_t>(), S->n, S->nnz, S->bsell_a, s))) return rc;
   if (S->bsell_a.nslices > 0) {
     const size_t tot = (size_t)9 * S->bsell_a.total + 64;
@@ -292,6 +295,7 @@ extern "C" int spai_system_schedule(const spai_system* S, spai_schedule* out) {
   out->sell = S->d->sell;
   out->fuse = S->d->fuse;
   out->block = S->d->block;
+  out->pair = S->d->pair;
   out->tuned = S->d->tuned;
   return SPAI_OK;
 }
@@ -319,14 +323,16 @@ extern "C" int spai_system_set_schedule(spai_system* S, const spai_schedule* sch
     return set_error(SPAI_ERR_INVALID, "tile_nnz must be in 1..%d (0: default)", (int)t0);
   if (sch->items_log2 < -4 || sch->items_log2 > 4) return set_error(SPAI_ERR_INVALID, "items_log2 must be in -4..4");
   if ((sch->staged != 0 && sch->staged != 1) || (sch->sell != 0 && sch->sell != 1) ||
-      (sch->fuse != 0 && sch->fuse != 1) || (sch->block != 0 && sch->block != 1))
-    return set_error(SPAI_ERR_INVALID, "staged, sell, fuse and block must be 0 or 1");
+      (sch->fuse != 0 && sch->fuse != 1) || (sch->block != 0 && sch->block != 1) ||
+      (sch->pair != 0 && sch->pair != 1))
+    return set_error(SPAI_ERR_INVALID, "staged, sell, fuse, block and pair must be 0 or 1");
   d.tile_nnz = sch->tile_nnz ? sch->tile_nnz : t0;
   d.items_log2 = sch->items_log2;
   d.staged = sch->staged;
   d.sell = sch->sell;
   d.fuse = sch->fuse;
   d.block = sch->block;
+  d.pair = sch->pair;
   d.tuned = 1;
   return SPAI_OK;
 }

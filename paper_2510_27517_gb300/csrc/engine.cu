@@ -72,6 +72,8 @@ struct EngSys {
   int32_t chunk_base;     // first chunk counter / chunk partial of this system
   int32_t fuse;           // 1: the G^T and G passes share one grid step (PH_P2F), ordered by item flags
   const int32_t* dep;     // fuse: per item, the first and last G^T-pass items whose rows its G rows reach
+  int32_t pair;           // 1: s with d and q with r stored as interleaved pairs (r[k], d[k] point at the
+                          // odd elements; q and s unused); kernel variants 1 and 2 only
   int64_t n;
   double eps;
   const double* b;
@@ -241,76 +243,115 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
 }
 
 // ---- per-phase operations: gather(col), pre(row) loads, fin(row, sum) ----
-template <class VT> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
-  const VT* s; const VT* dcur; VT* dnxt; VT* q; VT beta; bool first;
+// W is the element stride of the four paired vectors.  W = 1: s, d, q and r
+// are separate arrays.  W = 2: they are stored as interleaved pairs, s with d
+// (s_i at 2i, d_i at 2i + 1 of the same buffer) and q with r, so the passes
+// that gather two vectors at the same column (A: s and d; G^T: q and r) load
+// both with one 8-byte (float) or 16-byte (double) access, one L2 sector
+// request instead of two.  The arithmetic is the same for both strides.
+template <class VT> struct Pair2;
+template <> struct Pair2<float> { using T = float2; };
+template <> struct Pair2<double> { using T = double2; };
+template <class VT> __device__ __forceinline__ typename Pair2<VT>::T ldpair(const VT* p) {
+  return *reinterpret_cast<const typename Pair2<VT>::T*>(p);
+}
+
+template <class VT, int W> struct OpP1 {   // p = s + beta d;  d' = p;  q = A p;  p.q
+  const VT* s; const VT* dcur; VT* dnxt; VT* q; VT beta; bool first;   // W = 2: dcur = s + 1
   struct Pre { VT sv, dv; };
   __device__ VT gather(int c) const {
-    const VT sv = ldv(s + c);
-    return first ? sv : rfma(beta, ldv(dcur + c), sv);
+    if constexpr (W == 2) {
+      const auto v = ldpair(s + 2 * (int64_t)c);
+      return first ? v.x : rfma(beta, v.y, v.x);
+    } else {
+      const VT sv = ldv(s + c);
+      return first ? sv : rfma(beta, ldv(dcur + c), sv);
+    }
   }
-  __device__ Pre pre(int row) const { return Pre{ldv(s + row), first ? VT(0) : ldv(dcur + row)}; }
+  __device__ Pre pre(int row) const {
+    if constexpr (W == 2) {
+      const auto v = ldpair(s + 2 * (int64_t)row);
+      return Pre{v.x, first ? VT(0) : v.y};
+    } else {
+      return Pre{ldv(s + row), first ? VT(0) : ldv(dcur + row)};
+    }
+  }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     const VT pv = first ? p.sv : rfma(beta, p.dv, p.sv);
-    dnxt[row] = pv;
-    q[row] = sum;
+    dnxt[W * (int64_t)row] = pv;
+    q[W * (int64_t)row] = sum;
     p0 += (double)pv * (double)sum;
   }
 };
-template <class VT> struct OpP2 {   // x += alpha d;  r' = r - alpha q;  t = G^T r';  r'.r'
-  const VT* rcur; VT* rnxt; const VT* q; const VT* dcur; VT* x; VT* t; VT alpha;
+template <class VT, int W> struct OpP2 {   // x += alpha d;  r' = r - alpha q;  t = G^T r';  r'.r'
+  const VT* rcur; VT* rnxt; const VT* q; const VT* dcur; VT* x; VT* t; VT alpha;   // W = 2: rcur = q + 1
   struct Pre { VT xv, dv, rv, qv; };
-  __device__ VT gather(int c) const { return rfma(-alpha, ldv(q + c), ldv(rcur + c)); }
-  __device__ Pre pre(int row) const { return Pre{ldv(x + row), ldv(dcur + row), ldv(rcur + row), ldv(q + row)}; }
+  __device__ VT gather(int c) const {
+    if constexpr (W == 2) {
+      const auto v = ldpair(q + 2 * (int64_t)c);
+      return rfma(-alpha, v.x, v.y);
+    } else {
+      return rfma(-alpha, ldv(q + c), ldv(rcur + c));
+    }
+  }
+  __device__ Pre pre(int row) const {
+    if constexpr (W == 2) {
+      const auto v = ldpair(q + 2 * (int64_t)row);
+      return Pre{ldv(x + row), ldv(dcur + 2 * (int64_t)row), v.y, v.x};
+    } else {
+      return Pre{ldv(x + row), ldv(dcur + row), ldv(rcur + row), ldv(q + row)};
+    }
+  }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     x[row] = rfma(alpha, p.dv, p.xv);
     const VT rn = rfma(-alpha, p.qv, p.rv);
-    rnxt[row] = rn;
+    rnxt[W * (int64_t)row] = rn;
     t[row] = sum;
     p0 += (double)rn * (double)rn;
   }
 };
-template <class VT> struct OpApply1 {   // t = G^T r
+template <class VT, int W> struct OpApply1 {   // t = G^T r
   const VT* r; VT* t;
   struct Pre {};
-  __device__ VT gather(int c) const { return ldv(r + c); }
+  __device__ VT gather(int c) const { return ldv(r + W * (int64_t)c); }
   __device__ Pre pre(int) const { return Pre{}; }
   __device__ void fin(int row, VT sum, const Pre&, double&, double&) const { t[row] = sum; }
 };
-template <class VT> struct OpApply2 {   // s = G t + eps r;  r.s
+template <class VT, int W> struct OpApply2 {   // s = G t + eps r;  r.s
   const VT* t; const VT* r; VT* s; VT eps;
   struct Pre { VT rv; };
   __device__ VT gather(int c) const { return ldv(t + c); }
-  __device__ Pre pre(int row) const { return Pre{ldv(r + row)}; }
+  __device__ Pre pre(int row) const { return Pre{ldv(r + W * (int64_t)row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     const VT sv = rfma(eps, p.rv, sum);
-    s[row] = sv;
+    s[W * (int64_t)row] = sv;
     p0 += (double)p.rv * (double)sv;
   }
 };
-template <class VT> struct OpResid {   // r = b - A x;  r.r, b.b   (b float64)
+template <class VT, int W> struct OpResid {   // r = b - A x;  r.r, b.b   (b float64)
   const VT* x; const double* b; VT* r;
   struct Pre { double bv; };
   __device__ VT gather(int c) const { return ldv(x + c); }
   __device__ Pre pre(int row) const { return Pre{__ldg(b + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double& p1) const {
     const VT rv = rsub((VT)p.bv, sum);
-    r[row] = rv;
+    r[W * (int64_t)row] = rv;
     p0 += (double)rv * (double)rv;
     p1 += p.bv * p.bv;
   }
 };
-template <class VT> struct OpResidIn {   // r = rin - A e   (inner replacement, mixed)
+template <class VT, int W> struct OpResidIn {   // r = rin - A e   (inner replacement, mixed)
   const VT* e; const VT* rin; VT* r;
   struct Pre { VT iv; };
   __device__ VT gather(int c) const { return ldv(e + c); }
   __device__ Pre pre(int row) const { return Pre{ldv(rin + row)}; }
   __device__ void fin(int row, VT sum, const Pre& p, double& p0, double&) const {
     const VT rv = rsub(p.iv, sum);
-    r[row] = rv;
+    r[W * (int64_t)row] = rv;
     p0 += (double)rv * (double)rv;
   }
 };
-template <class VT> struct OpResid64 {   // r64 = b - A64 x64;  r = rin = (VT) r64;  e = 0
+template <class VT, int W> struct OpResid64 {   // r64 = b - A64 x64;  r = rin = (VT) r64;  e = 0
   const double* x64; const double* b; VT* r; VT* rin; VT* e;
   struct Pre { double bv; };
   __device__ double gather(int c) const { return ldv(x64 + c); }
@@ -318,7 +359,7 @@ template <class VT> struct OpResid64 {   // r64 = b - A64 x64;  r = rin = (VT) r
   __device__ void fin(int row, double sum, const Pre& p, double& p0, double& p1) const {
     const double r64 = __dsub_rn(p.bv, sum);
     const VT r32 = (VT)r64;
-    r[row] = r32;
+    r[W * (int64_t)row] = r32;
     rin[row] = r32;
     e[row] = VT(0);
     p0 += r64 * r64;
@@ -702,18 +743,20 @@ __device__ __forceinline__ void run_groups(bool piped, Pipe& P, const int32_t* t
 // through the ring, the 3 x 3 block layout, row maps).  A launch runs the
 // smallest variant its members need: each extra path costs the SELL-32 loop
 // registers and time.
-template <class VT, class GT, bool MIXED, int KV>
-__device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P, void* sbuf,
-                         double* red, double& p0, double& p1, uint64_t limit_ns, int* err, int rc) {
+// W = 2 (paired vectors) only in variants 1 and 2.
+template <class VT, class GT, bool MIXED, int KV, int W>
+__device__ void run_item_w(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P, void* sbuf,
+                           double* red, double& p0, double& p1, uint64_t limit_ns, int* err, int rc) {
   constexpr bool CSR = KV == 2;
   const int dc = st.dc;
   VT* r_cur = reinterpret_cast<VT*>(S.r[rc]);
   VT* r_nxt = reinterpret_cast<VT*>(S.r[rc ^ 1]);
   VT* d_cur = reinterpret_cast<VT*>(S.d[dc]);
   VT* d_nxt = reinterpret_cast<VT*>(S.d[dc ^ 1]);
-  VT* q_v = reinterpret_cast<VT*>(S.q);
+  // paired: q shares r[rc]'s buffer (q_i at 2i, r_i at 2i + 1), s shares d[dc]'s
+  VT* q_v = W == 2 ? r_cur - 1 : reinterpret_cast<VT*>(S.q);
   VT* t = reinterpret_cast<VT*>(S.t);
-  VT* s = reinterpret_cast<VT*>(S.s);
+  VT* s = W == 2 ? d_cur - 1 : reinterpret_cast<VT*>(S.s);
   VT* xv = MIXED ? reinterpret_cast<VT*>(S.e) : reinterpret_cast<VT*>(S.x);  // iterate
   VT* rin = reinterpret_cast<VT*>(S.rin);
   const VT* aval = reinterpret_cast<const VT*>(S.val[MAT_A]);
@@ -736,22 +779,22 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
     if constexpr (CSR) switch (ph) {
       case PH_P1:
         q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n,
-                               OpP1<VT>{s, d_cur, d_nxt, q_v, beta, st.first != 0});
+                               OpP1<VT, W>{s, d_cur, d_nxt, q_v, beta, st.first != 0});
         break;
       case PH_P2:
         q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_GT], gtval, g0, g1, n,
-                               OpP2<VT>{r_cur, r_nxt, q_v, d_cur, xv, t, alpha});
+                               OpP2<VT, W>{r_cur, r_nxt, q_v, d_cur, xv, t, alpha});
         break;
       case PH_APPLY1:
-        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_GT], gtval, g0, g1, n, OpApply1<VT>{r_cur, t});
+        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_GT], gtval, g0, g1, n, OpApply1<VT, W>{r_cur, t});
         break;
       case PH_APPLY2:
-        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_G], gval, g0, g1, n, OpApply2<VT>{t, r_cur, s, eps});
+        q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_G], gval, g0, g1, n, OpApply2<VT, W>{t, r_cur, s, eps});
         break;
       case PH_RESID0:
       case PH_RESID:
-        if (!MIXED) q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n, OpResid<VT>{xv, S.b, r_cur});
-        else q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n, OpResidIn<VT>{xv, rin, r_cur});
+        if (!MIXED) q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n, OpResid<VT, W>{xv, S.b, r_cur});
+        else q = direct_bslices<VT>(tl, S.sptr[m], S.ci[MAT_A], aval, g0, g1, n, OpResidIn<VT, W>{xv, rin, r_cur});
         break;
       default:
         break;
@@ -763,39 +806,39 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
 
   switch (ph) {
     case PH_P1: {
-      OpP1<VT> op{s, d_cur, d_nxt, q_v, beta, st.first != 0};
+      OpP1<VT, W> op{s, d_cur, d_nxt, q_v, beta, st.first != 0};
       run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_P2: {
-      OpP2<VT> op{r_cur, r_nxt, q_v, d_cur, xv, t, alpha};
+      OpP2<VT, W> op{r_cur, r_nxt, q_v, d_cur, xv, t, alpha};
       run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_APPLY1: {
-      OpApply1<VT> op{r_cur, t};
+      OpApply1<VT, W> op{r_cur, t};
       run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_GT], S.ci[MAT_GT], gtval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_APPLY2: {
-      OpApply2<VT> op{t, r_cur, s, eps};
+      OpApply2<VT, W> op{t, r_cur, s, eps};
       run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_G], S.ci[MAT_G], gval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       break;
     }
     case PH_RESID0:
     case PH_RESID: {
       if (!MIXED) {
-        OpResid<VT> op{xv, S.b, r_cur};
+        OpResid<VT, W> op{xv, S.b, r_cur};
         run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       } else {
-        OpResidIn<VT> op{xv, rin, r_cur};
+        OpResidIn<VT, W> op{xv, rin, r_cur};
         run_groups<VT, CSR>(piped, P, tl, S.rp[MAT_A], S.ci[MAT_A], aval, g0, g1, sbuf, red, op, p0, p1, limit_ns, err, sp, n, srow);
       }
       break;
     }
     case PH_RESID64: {
       if constexpr (MIXED) {
-        OpResid64<VT> op{S.x, S.b, r_cur, rin, xv};
+        OpResid64<VT, W> op{S.x, S.b, r_cur, rin, xv};
         if (rpu > 1) {  // the rows of slices [tl[g0], tl[g1]) over the CSR copy of A
           const int r0 = __ldg(tl + g0) * rpu, r1 = (int)min((int64_t)__ldg(tl + g1) * rpu, n);
           if (r0 < r1) {
@@ -819,7 +862,7 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
       const int r0 = __ldg(tl + g0) * rpu;
       const int r1 = (int)min((int64_t)__ldg(tl + g1) * rpu, n);
       for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-        if (ph == PH_P2X) xv[row] = rfma(alpha, ldv(d_cur + row), ldv(xv + row));
+        if (ph == PH_P2X) xv[row] = rfma(alpha, ldv(d_cur + W * (int64_t)row), ldv(xv + row));
         else if (ph == PH_XUPD) {
           S.x[row] = __dadd_rn(ldv(S.x + row), (double)ldv(xv + row));
           xv[row] = VT(0);
@@ -831,6 +874,33 @@ __device__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, in
     default:
       break;
   }
+}
+
+// The paired path is a separate function so that the kernel's own loop keeps
+// the registers of the separate-vector path (one call per work item).
+template <class VT, class GT, bool MIXED, int KV>
+__device__ __noinline__ void run_item_pair(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P,
+                                           void* sbuf, double* red, double* pp, uint64_t limit_ns, int* err, int rc) {
+  double p0 = pp[0], p1 = pp[1];
+  run_item_w<VT, GT, MIXED, KV, 2>(ph, S, st, g0, g1, P, sbuf, red, p0, p1, limit_ns, err, rc);
+  pp[0] = p0;
+  pp[1] = p1;
+}
+
+template <class VT, class GT, bool MIXED, int KV>
+__device__ __forceinline__ void run_item(int ph, const EngSys& S, const EngState& st, int g0, int g1, Pipe& P,
+                                         void* sbuf, double* red, double& p0, double& p1, uint64_t limit_ns, int* err,
+                                         int rc) {
+  if constexpr (KV >= 1) {
+    if (S.pair) {
+      double pp[2] = {p0, p1};
+      run_item_pair<VT, GT, MIXED, KV>(ph, S, st, g0, g1, P, sbuf, red, pp, limit_ns, err, rc);
+      p0 = pp[0];
+      p1 = pp[1];
+      return;
+    }
+  }
+  run_item_w<VT, GT, MIXED, KV, 1>(ph, S, st, g0, g1, P, sbuf, red, p0, p1, limit_ns, err, rc);
 }
 
 // State machine of one system; runs once per phase in the block that
@@ -1278,7 +1348,7 @@ int engine_tile_nnz(int32_t max_row) {
 size_t engine_work_bytes(int64_t n, bool mixed) {
   const size_t vsz = mixed ? sizeof(float) : sizeof(double);
   const size_t stride = ((n * vsz + 255) / 256) * 256;
-  return stride * (mixed ? 9 : 7) + 256;
+  return stride * (mixed ? 11 : 9) + 256;  // room for the paired layout (r, d buffers twice as long)
 }
 
 // A set of systems advanced together by the persistent kernel.  Members keep
@@ -1436,6 +1506,7 @@ class EngineBatch {
         if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2) csr_ring = true;  // the full kernel
         if (e.srow[mm]) rmap = true;
       }
+      if (A.pair) rmap = true;  // paired vectors: variant 1 or 2
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
       const int kg = engine_scale_k(engine_items_k(ng, grid_max_), A.items_log2, ng);
@@ -1453,10 +1524,18 @@ class EngineBatch {
       const size_t vsz = mixed_ ? sizeof(float) : sizeof(double);
       const size_t stride = ((A.n * vsz + 255) / 256) * 256;
       char* base = static_cast<char*>(mb.work);
-      e.r[0] = base; e.r[1] = base + stride;
-      e.d[0] = base + 2 * stride; e.d[1] = base + 3 * stride;
-      e.q = base + 4 * stride; e.t = base + 5 * stride; e.s = base + 6 * stride;
-      if (mixed_) { e.e = base + 7 * stride; e.rin = base + 8 * stride; }
+      if (A.pair) {  // pair buffers (q, r[0]), (q, r[1]), (s, d[0]), (s, d[1]) of 2n values each
+        e.pair = 1;
+        e.r[0] = base + vsz; e.r[1] = base + 2 * stride + vsz;
+        e.d[0] = base + 4 * stride + vsz; e.d[1] = base + 6 * stride + vsz;
+        e.t = base + 8 * stride;
+        if (mixed_) { e.e = base + 9 * stride; e.rin = base + 10 * stride; }
+      } else {
+        e.r[0] = base; e.r[1] = base + stride;
+        e.d[0] = base + 2 * stride; e.d[1] = base + 3 * stride;
+        e.q = base + 4 * stride; e.t = base + 5 * stride; e.s = base + 6 * stride;
+        if (mixed_) { e.e = base + 7 * stride; e.rin = base + 8 * stride; }
+      }
       e.history = mb.history;
       e.history_len = mb.history_len;
       e.lanczos = mb.lanczos;

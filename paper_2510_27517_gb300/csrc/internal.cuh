@@ -126,6 +126,7 @@ struct SystemData {
   int32_t sell = 1;          // 1: SELL-32 layout for matrices that have one, 0: CSR row groups
   int32_t fuse = 1;          // 1: G^T and G passes in one grid step ordered by item flags
   int32_t block = 1;         // 1: the 3 x 3 block layout for matrices that have it (A and G)
+  int32_t pair = 0;          // 1: s with d and q with r stored as interleaved pairs (set for sorted rows)
   int32_t autotune = 0;      // pick the schedule by timing candidates on the first solve
   int32_t tuned = 0;
   TileSet tiles;

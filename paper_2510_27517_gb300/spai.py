@@ -59,7 +59,8 @@ class _Res(C.Structure):
 
 class _Sched(C.Structure):
     _fields_ = [("tile_nnz", C.c_int32), ("items_log2", C.c_int32), ("staged", C.c_int32), ("sell", C.c_int32),
-                ("fuse", C.c_int32), ("block", C.c_int32), ("tuned", C.c_int32)]
+                ("fuse", C.c_int32), ("block", C.c_int32), ("pair", C.c_int32),
+                ("tuned", C.c_int32)]
 
 
 class _AdamW(C.Structure):
@@ -283,8 +284,11 @@ class System(_Handle):
         _check(lib().spai_system_info(self.h, C.byref(lo)))
         return {k: getattr(lo, k) for k, _ in _Layout._fields_}
 
-    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1, fuse=1, block=1):
-        sc = _Sched(tile_nnz, items_log2, staged, sell, fuse, block, 0)
+    def set_schedule(self, tile_nnz=0, items_log2=0, staged=1, sell=1, fuse=1, block=1, pair=None):
+        """pair=None: paired vectors where the rows were sorted by length (the default at creation)."""
+        if pair is None:
+            pair = 1 if self.layout()["sell_sorted"] else 0
+        sc = _Sched(tile_nnz, items_log2, staged, sell, fuse, block, pair, 0)
         _check(lib().spai_system_set_schedule(self.h, C.byref(sc)))
 
 

@@ -282,7 +282,8 @@ def test_autotuned_schedule_fixed_and_batch_consistent(spai_lib):
                                    dict(sell=1, fuse=0), dict(sell=0, staged=0, fuse=0),
                                    dict(matrix="graph", sell=1), dict(matrix="graph", sell=1, fuse=0),
                                    dict(matrix="graph", sell=1, tile_nnz=300, items_log2=1),
-                                   dict(matrix="graph", sell=0, staged=1)])
+                                   dict(matrix="graph", sell=0, staged=1), dict(matrix="graph", sell=1, pair=0),
+                                   dict(sell=1, pair=1), dict(sell=0, staged=1, pair=1)])
 def test_every_schedule_matches_oracle(spai_lib, sched):
     # SELL-32 slices (rows in their own order for the stencil; ordered by
     # length within windows for the graph Laplacian, whose rows are too
@@ -302,6 +303,7 @@ def test_every_schedule_matches_oracle(spai_lib, sched):
     lay = S.layout()
     assert lay["sell_slices"] > 0 and lay["sell_sorted"] == (1 if graph else 0)
     assert lay["sell_total"] * 4 <= A.nnz * 5
+    assert S.schedule()["pair"] == (1 if graph else 0)  # paired vectors by default for sorted rows
     S.set_schedule(**sched)
     assert S.schedule()["tuned"] == 1
     P = spai.build_pattern(dA, spai.PATTERN_FULL)
@@ -331,7 +333,7 @@ def test_set_schedule_rejects_out_of_range(spai_lib):
     spai = spai_lib
     A = W.poisson2d(16)
     S = spai.system_create(upload(spai, A))
-    for bad in (dict(tile_nnz=5000), dict(items_log2=5), dict(staged=2), dict(sell=-1), dict(fuse=2)):
+    for bad in (dict(tile_nnz=5000), dict(items_log2=5), dict(staged=2), dict(sell=-1), dict(fuse=2), dict(pair=2)):
         with pytest.raises(spai.SpaiError):
             S.set_schedule(**bad)
 
@@ -399,13 +401,18 @@ def test_host_buffer_solve_poisson64(spai_lib):
         assert pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x, b) <= 1e-8
 
 
-@pytest.mark.parametrize("case", ["gnn_sell_mixed", "gnn_csr_f64", "fsai_upper", "graph_direct", "batch"])
-def test_fused_step_is_bit_identical(spai_lib, case):
-    # the G^T and G passes in one grid step, ordered by item flags, run the
-    # same arithmetic as one grid step per pass: identical iterates, residual
-    # histories and iteration counts, for SELL-32 and CSR (staged and direct)
-    # layouts, a factor whose G and G^T have different row structure (FSAI on
-    # the upper triangle) and a batch
+@pytest.mark.parametrize("flag", ["fuse", "pair"])
+@pytest.mark.parametrize("case", ["gnn_sell_mixed", "gnn_csr_f64", "fsai_upper", "graph_direct", "graph_sell",
+                                  "batch"])
+def test_schedule_flags_are_bit_identical(spai_lib, case, flag):
+    # fuse: the G^T and G passes in one grid step, ordered by item flags, run
+    # the same arithmetic as one grid step per pass.  pair: s with d and q
+    # with r stored as interleaved pairs (one load per gathered pair) run the
+    # same arithmetic as separate vectors.  Identical iterates, residual
+    # histories and iteration counts, for SELL-32 (rows in order and sorted by
+    # length) and CSR (staged and direct) layouts, a factor whose G and G^T
+    # have different row structure (FSAI on the upper triangle) and a batch
+    # (pair: only every other member paired, so one launch runs both layouts)
     spai = spai_lib
 
     def build(A, kind, seed):
@@ -437,18 +444,21 @@ def test_fused_step_is_bit_identical(spai_lib, case):
         specs = [(W.poisson2d(48), "fsai", dict(sell=0, staged=1))]
     elif case == "graph_direct":
         specs = [(W.graph_laplacian(3000, 24000, seed=5), "graph", dict(sell=0, staged=0))]
+    elif case == "graph_sell":
+        specs = [(W.graph_laplacian(5000, 40000, seed=9), "graph", dict(sell=1))]
     else:
         specs = [(W.graph_laplacian(2000, 16000, seed=6), "graph", dict(sell=0, staged=1)),
                  (W.aniso2d(60, 30.0, 0.3), "graph", dict(sell=1)),
                  (W.graph_laplacian(500, 4000, seed=7), "graph", dict(sell=0, staged=0)),
                  (W.graph_laplacian(4000, 32000, seed=8), "graph", dict(sell=1))]
     runs = {}
-    for fuse in (0, 1):
+    for on in (0, 1):
         systems, preconds, bs, xs, hs, prec = [], [], [], [], [], None
         for i, (A, kind, sched) in enumerate(specs):
             dA, M, prec = build(A, kind, i)
             S = spai.system_create(dA)
-            S.set_schedule(fuse=fuse, **sched)
+            S.set_schedule(**{flag: on if (flag == "fuse" or len(specs) == 1 or i % 2 == 0) else 0}, **sched)
+            assert S.schedule()[flag] == (on if (flag == "fuse" or len(specs) == 1 or i % 2 == 0) else 0)
             systems.append(S), preconds.append(M)
             bs.append(torch.tensor(W.rhs_uniform(A.n, 70 + i), device="cuda"))
             xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
@@ -458,7 +468,7 @@ def test_fused_step_is_bit_identical(spai_lib, case):
             hs = [h[:r[0]["history_written"]].clone()]
         else:
             r = spai.pcg_solve_batched(systems, preconds, bs, xs, precision=prec)
-        runs[fuse] = (r, [x.clone() for x in xs], hs)
+        runs[on] = (r, [x.clone() for x in xs], hs)
     (r0, x0, h0), (r1, x1, h1) = runs[0], runs[1]
     for a, b in zip(r0, r1):
         assert a["status"] == 0 and b["status"] == 0
