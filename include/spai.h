@@ -362,7 +362,10 @@ int spai_system_schedule(const spai_system* S, spai_schedule* out);
 
 /* Fixes the schedule (no autotuning afterwards).  SPAI_ERR_INVALID for a
  * field out of range (tile_nnz above the largest group that fits the
- * staging buffer for this matrix, items_log2 outside -4..4, flags not 0/1). */
+ * staging buffer for this matrix, items_log2 outside -4..4, flags not 0/1).
+ * Takes effect for solves started afterwards; a request already submitted to
+ * a server keeps the vector layout (`pair`) it was submitted with.  Not to be
+ * called while a solve of the system runs on another thread. */
 int spai_system_set_schedule(spai_system* S, const spai_schedule* sch);
 
 /* Layout facts of a system (for callers and tests): sizes, the longest row,

@@ -32,6 +32,7 @@
 // partials in a fixed order and computes the system's next state.  Results
 // therefore depend only on the system and its schedule, not on the other
 // systems in the launch or on which block ran which tile.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1058,12 +1059,14 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
     EngState* nxt = par ? a.st0 : a.st1;
     const unsigned epoch = (unsigned)(slot0 + slots) + 1u;
     // Pass 0 runs every system's phase; pass 1 only the G pass of fused
-    // steps (PH_P2F), whose items wait for the flags pass 0 published.  Item
-    // v runs in block v % grid in both passes.
+    // steps (PH_P2F), whose items wait for the flags pass 0 published.  The
+    // item at table position p runs in block p % grid in both passes; a
+    // block finishes its pass-0 items before it waits in pass 1.
     for (int pass = 0; pass < 2; ++pass) {
       int cached = -1;
       for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
         const int sid = __ldg(a.item_sys + it);
+        if (sid < 0) continue;  // a hole of the last round
         const int v = __ldg(a.item_tile + it);
         if (sid != cached) {
           if (threadIdx.x == 0) load_state(cur + sid, &s_st);
@@ -1345,10 +1348,10 @@ int engine_tile_nnz(int32_t max_row) {
   return kCap - max_row + 1;
 }
 
-size_t engine_work_bytes(int64_t n, bool mixed) {
+size_t engine_work_bytes(int64_t n, bool mixed, bool pair) {
   const size_t vsz = mixed ? sizeof(float) : sizeof(double);
   const size_t stride = ((n * vsz + 255) / 256) * 256;
-  return stride * (mixed ? 11 : 9) + 256;  // room for the paired layout (r, d buffers twice as long)
+  return stride * ((mixed ? 9 : 7) + (pair ? 2 : 0)) + 256;  // paired: r and d buffers twice as long
 }
 
 // A set of systems advanced together by the persistent kernel.  Members keep
@@ -1361,7 +1364,8 @@ class EngineBatch {
     PrecondData* M;
     const double* b;
     double* x;
-    void* work;              // engine_work_bytes(n, mixed) bytes of device memory
+    void* work;              // engine_work_bytes(n, mixed, pair) bytes of device memory
+    int32_t pair;            // vector layout of `work` (the system's schedule when the solve began)
     double* history;
     int64_t history_len;
     double* lanczos;
@@ -1506,7 +1510,7 @@ class EngineBatch {
         if ((!e.fmt[mm] && e.fits[mm]) || e.fmt[mm] == 2) csr_ring = true;  // the full kernel
         if (e.srow[mm]) rmap = true;
       }
-      if (A.pair) rmap = true;  // paired vectors: variant 1 or 2
+      if (mb.pair) rmap = true;  // paired vectors: variant 1 or 2
       // work items depend only on the system and the kernel's full grid, so a
       // system's reductions are identical alone and in any batch
       const int kg = engine_scale_k(engine_items_k(ng, grid_max_), A.items_log2, ng);
@@ -1524,7 +1528,7 @@ class EngineBatch {
       const size_t vsz = mixed_ ? sizeof(float) : sizeof(double);
       const size_t stride = ((A.n * vsz + 255) / 256) * 256;
       char* base = static_cast<char*>(mb.work);
-      if (A.pair) {  // pair buffers (q, r[0]), (q, r[1]), (s, d[0]), (s, d[1]) of 2n values each
+      if (mb.pair) {  // pair buffers (q, r[0]), (q, r[1]), (s, d[0]), (s, d[1]) of 2n values each
         e.pair = 1;
         e.r[0] = base + vsz; e.r[1] = base + 2 * stride + vsz;
         e.d[0] = base + 4 * stride + vsz; e.d[1] = base + 6 * stride + vsz;
@@ -1546,16 +1550,56 @@ class EngineBatch {
     if (items >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
     smem_ = engine_smem_bytes(mixed_, csr_ring);
     kfn_ = kfns_[csr_ring ? 2 : (rmap ? 1 : 0)];
-    std::vector<int32_t> isys(items), itile(items);
-    for (int i = 0; i < nsys; ++i)
-      for (int v = 0; v < hs[i].nitems; ++v) {
-        isys[hs[i].item_base + v] = i;
-        itile[hs[i].item_base + v] = v;
+    int grid = grid_max_;
+    if (grid_override > 0 && grid_override < grid) grid = grid_override;
+    if (grid > items) grid = (int)items;
+    if (grid < 1) grid = 1;
+    // Positions of the items in the launch table: block b runs positions b,
+    // b + grid, b + 2 grid, ...  Items are dealt in order of decreasing size
+    // (entries of the three matrices in their groups) in a snake, blocks 0 ..
+    // grid - 1 and then grid - 1 .. 0, so that members of very different
+    // sizes load every block about equally; holes of the last round hold
+    // system -1.  Which block runs an item does not change its arithmetic.
+    // One system alone in at most one round keeps item v at position v.
+    const int64_t rounds = (items + grid - 1) / grid;
+    const int64_t npos = rounds * grid;
+    if (npos >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
+    std::vector<int32_t> isys(npos, -1), itile(npos, 0);
+    {
+      std::vector<int64_t> ord(items);
+      std::vector<double> w(items);
+      for (int i = 0; i < nsys; ++i) {
+        const EngSys& e = hs[i];
+        const double ent[3] = {(double)members[i].S->nnz, (double)members[i].M->P->nnz,
+                               (double)members[i].M->P->nnz};
+        for (int v = 0; v < e.nitems; ++v) {
+          double wt = 0.0;
+          for (int mm = 0; mm < 3; ++mm) {
+            const int64_t g = std::min<int64_t>(e.kgroups[mm], (int64_t)e.ntiles[mm] - (int64_t)v * e.kgroups[mm]);
+            if (g > 0 && e.ntiles[mm] > 0) wt += (double)g * ent[mm] / e.ntiles[mm];
+          }
+          ord[e.item_base + v] = e.item_base + v;
+          w[e.item_base + v] = wt;
+        }
       }
+      std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return w[x] > w[y]; });
+      std::vector<int32_t> owner(items), idx(items);
+      for (int i = 0; i < nsys; ++i)
+        for (int v = 0; v < hs[i].nitems; ++v) {
+          owner[hs[i].item_base + v] = i;
+          idx[hs[i].item_base + v] = v;
+        }
+      for (int64_t j = 0; j < items; ++j) {
+        const int64_t r = j / grid, c = j % grid;
+        const int64_t pos = r * grid + ((r & 1) ? grid - 1 - c : c);
+        isys[pos] = owner[ord[j]];
+        itile[pos] = idx[ord[j]];
+      }
+    }
     std::vector<EngState> hst(nsys);
     for (int i = 0; i < nsys; ++i) hst[i] = members[i].st;
     const size_t sz_sys = sizeof(EngSys) * nsys, sz_st = sizeof(EngState) * nsys;
-    const size_t sz_items = sizeof(int32_t) * items, sz_part = sizeof(double) * 2 * items;
+    const size_t sz_items = sizeof(int32_t) * npos, sz_part = sizeof(double) * 2 * items;
     const size_t sz_cnt = sizeof(unsigned) * nsys;
     const size_t sz_cpart = sizeof(double) * 2 * chunks, sz_ccnt = sizeof(unsigned) * chunks;
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
@@ -1605,7 +1649,7 @@ class EngineBatch {
     args_.nsys = nsys;
     args_.item_sys = reinterpret_cast<const int32_t*>(tb + off_is);
     args_.item_tile = reinterpret_cast<const int32_t*>(tb + off_it);
-    args_.n_items = (int32_t)items;
+    args_.n_items = (int32_t)npos;
     args_.partial = reinterpret_cast<double*>(tb + off_part);
     args_.cnt = reinterpret_cast<unsigned*>(tb + off_cnt);
     args_.cpartial = reinterpret_cast<double*>(tb + off_cpart);
@@ -1627,10 +1671,7 @@ class EngineBatch {
     args_.o.max_outer = opts_.max_outer > 0 ? opts_.max_outer : 0;
     args_.o.mixed = mixed_ ? 1 : 0;
     args_.limit_ns = 2000000000ull;  // 2 s per device-side wait
-    grid_ = grid_max_;
-    if (grid_override > 0 && grid_override < grid_) grid_ = grid_override;
-    if (grid_ > items) grid_ = (int)items;
-    if (grid_ < 1) grid_ = 1;
+    grid_ = grid;
     slots_ = 0;
     return SPAI_OK;
   }
@@ -1823,13 +1864,14 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   std::vector<DevMem> ws(nsys);
   std::vector<EngineBatch::Member> mem(nsys);
   for (int i = 0; i < nsys; ++i) {
-    if ((rc = ws[i].alloc(engine_work_bytes(S[i]->n, mixed), s))) return rc;
+    if ((rc = ws[i].alloc(engine_work_bytes(S[i]->n, mixed, S[i]->pair != 0), s))) return rc;
     EngineBatch::Member& m = mem[i];
     m.S = S[i];
     m.M = M[i];
     m.b = b[i];
     m.x = x[i];
     m.work = ws[i].p;
+    m.pair = S[i]->pair;
     m.history = (nsys == 1 && o->record_history) ? o->history : nullptr;
     m.history_len = (nsys == 1 && o->record_history) ? o->history_len : 0;
     m.lanczos = (nsys == 1 && o->lanczos && o->lanczos_len > 0) ? o->lanczos : nullptr;
@@ -1979,20 +2021,6 @@ int engine_tune(SystemData* S, PrecondData* M, bool mixed, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 namespace spai {
 
-struct SessionMember {
-  SystemData* S;
-  PrecondData* M;
-  const double* b;
-  double* x;
-  void* work;
-  std::vector<unsigned char> state;  // empty: start a new solve
-};
-struct SessionView {
-  bool done;
-  int status;
-  int64_t iters;
-  int outer;
-};
 struct EngineSession {
   EngineBatch batch;
   bool mixed;
@@ -2023,6 +2051,7 @@ int session_set(EngineSession* es, std::vector<SessionMember>& members) {
     m.b = sm.b;
     m.x = sm.x;
     m.work = sm.work;
+    m.pair = sm.pair;
     m.history = nullptr;
     m.history_len = 0;
     m.lanczos = nullptr;

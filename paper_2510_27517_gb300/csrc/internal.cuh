@@ -166,6 +166,36 @@ int bsell_values(const SellData& L, const int32_t* rp, int64_t n, const void* va
 int matrix_abs_mean(const double* val, int64_t nnz, double* out, cudaStream_t s);
 int num_sms();
 
+// Bytes of engine workspace of one system (its iteration vectors); `pair`:
+// the interleaved layout of s with d and q with r (two vectors longer).
+size_t engine_work_bytes(int64_t n, bool mixed, bool pair);
+
+// Session interface of the engine, used by the server: a batch whose members
+// carry their state (an opaque block of engine_state_bytes()) across launches.
+struct SessionMember {
+  SystemData* S;
+  PrecondData* M;
+  const double* b;
+  double* x;
+  void* work;                        // engine_work_bytes(S->n, mixed, pair) bytes
+  int32_t pair;                      // the vector layout `work` was sized and started for
+  std::vector<unsigned char> state;  // empty: start a new solve
+};
+struct SessionView {
+  bool done;
+  int status;
+  int64_t iters;
+  int outer;
+};
+struct EngineSession;
+size_t engine_state_bytes();
+int session_create(bool mixed, int gtype, const spai_pcg_opts& o, cudaStream_t s, EngineSession** out);
+int session_set(EngineSession* es, std::vector<SessionMember>& members);
+int session_launch(EngineSession* es, int max_slots);
+int session_live(EngineSession* es);
+int session_read(EngineSession* es, std::vector<SessionMember>& members, std::vector<SessionView>& views);
+void session_destroy(EngineSession* es);
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------

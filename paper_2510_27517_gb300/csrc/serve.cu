@@ -24,28 +24,6 @@
 
 namespace spai {
 
-struct SessionMember {
-  SystemData* S;
-  PrecondData* M;
-  const double* b;
-  double* x;
-  void* work;
-  std::vector<unsigned char> state;
-};
-struct SessionView {
-  bool done;
-  int status;
-  int64_t iters;
-  int outer;
-};
-struct EngineSession;
-int session_create(bool mixed, int gtype, const spai_pcg_opts& o, cudaStream_t s, EngineSession** out);
-int session_set(EngineSession* es, std::vector<SessionMember>& members);
-int session_launch(EngineSession* es, int max_slots);
-int session_live(EngineSession* es);
-int session_read(EngineSession* es, std::vector<SessionMember>& members, std::vector<SessionView>& views);
-void session_destroy(EngineSession* es);
-size_t engine_work_bytes(int64_t n, bool mixed);
 int engine_true_residuals(int nsys, SystemData* const* S, const double* const* b, double* const* x, double* out,
                           cudaStream_t s);
 
@@ -58,6 +36,7 @@ struct Request {
   double* xh = nullptr;
   double t_submit = 0, t_admit = 0;
   size_t bytes = 0;
+  int32_t pair = 0;  // vector layout of the workspace (the system's schedule at submission)
   DevMem buf;  // b, x, engine workspace
   std::vector<unsigned char> state;
 };
@@ -104,6 +83,7 @@ int ServerImpl::loop(cudaStream_t s) {
     m.b = r.buf.as<double>();
     m.x = reinterpret_cast<double*>(r.buf.as<char>() + nb);
     m.work = r.buf.as<char>() + 2 * nb;
+    m.pair = r.pair;
     m.state = r.state;
     return m;
   };
@@ -122,7 +102,7 @@ int ServerImpl::loop(cudaStream_t s) {
         queue.pop_front();
         SystemData& S = *systems[r->sys].first;
         const size_t nb = S.n * sizeof(double);
-        if ((rc = r->buf.alloc(2 * nb + engine_work_bytes(S.n, mixed), s))) break;
+        if ((rc = r->buf.alloc(2 * nb + engine_work_bytes(S.n, mixed, r->pair != 0), s))) break;
         double* bd = r->buf.as<double>();
         if (cudaMemcpyAsync(bd, r->bh, nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(reinterpret_cast<char*>(bd) + nb, 0, nb, s) != cudaSuccess) {
@@ -279,7 +259,8 @@ extern "C" int spai_server_submit(spai_server* srv, int64_t sys_id, const double
     if (sys_id < 0 || sys_id >= (int64_t)I.systems.size()) return set_error(SPAI_ERR_NOT_FOUND, "unknown system id");
     const int64_t n = I.systems[sys_id].first->n;
     const bool mixed = I.cfg.opts.precision == SPAI_PREC_MIXED;
-    r->bytes = 2 * n * sizeof(double) + engine_work_bytes(n, mixed);
+    r->pair = I.systems[sys_id].first->pair;
+    r->bytes = 2 * n * sizeof(double) + engine_work_bytes(n, mixed, r->pair != 0);
     if ((int64_t)r->bytes > I.cfg.hbm_cap_bytes)
       return set_error(SPAI_ERR_TOO_LARGE, "request needs %zu device bytes, cap is %lld", r->bytes,
                        (long long)I.cfg.hbm_cap_bytes);
