@@ -148,6 +148,9 @@ constexpr int kMaxK = 64;     // groups per work item at most
 constexpr int kWarpE = 256;   // entries per warp product chunk
 constexpr int kAlignE = 8;    // bulk copies start at multiples of 8 entries (16 B for every type)
 constexpr int kSlicesInReg = 63;  // SELL groups of up to this many slices keep their offsets in registers
+// GridSync::err value of a launch-table entry out of range (never expected:
+// the kernel skips the entry and the host reports it).
+constexpr int kErrTable = -100;
 
 // y_row = sum over the row's entries of val * op.gather(col), in stored
 // order, then op.fin(row, y_row, op.pre(row)).  Rows are processed in groups
@@ -1038,7 +1041,7 @@ template <class VT, class GT, bool MIXED, int KV>
 __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   using MVmax = typename std::conditional<MIXED, float, double>::type;
   __shared__ double red[64];
-  __shared__ int sflag, s_last;
+  __shared__ int sflag, s_last, s_sys;
   __shared__ EngState s_st;
 
   Pipe P;
@@ -1052,6 +1055,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
   __syncthreads();
 
   const int slot0 = *(volatile int*)&a.gs->slot;
+  const int npos = *(volatile int*)&a.gs->npos;  // fixed for the launch (re-dealt only between launches)
   int slots = 0;
   for (;;) {
     const int par = (slot0 + slots) & 1;
@@ -1064,11 +1068,18 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
     // block finishes its pass-0 items before it waits in pass 1.
     for (int pass = 0; pass < 2; ++pass) {
       int cached = -1;
-      for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+      for (int it = blockIdx.x; it < npos; it += gridDim.x) {
         const int sid = __ldg(a.item_sys + it);
         if (sid < 0) continue;  // a hole of the last round
         const int v = __ldg(a.item_tile + it);
+        if (sid >= a.nsys || v < 0 || v >= a.sys[sid].nitems) {  // a corrupt table entry: flag it, skip it
+          if (threadIdx.x == 0) atomicCAS(&a.gs->err, 0, kErrTable);
+          continue;
+        }
         if (sid != cached) {
+          // every thread has read the previous system's state (the skips
+          // below leave an item without the closing barrier)
+          __syncthreads();
           if (threadIdx.x == 0) load_state(cur + sid, &s_st);
           __syncthreads();
           cached = sid;
@@ -1114,6 +1125,9 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
           s_last = (prev == (unsigned)(ch_size - 1)) ? 1 : 0;
         }
         __syncthreads();
+        // s_last is read by every thread here and written again only after
+        // the next item's reduction barriers; the system decision goes to
+        // s_sys, so no warp can see it change before it has read it
         if (s_last) {
           // this block completed chunk `ch`: sum its item partials (one warp, fixed tree)
           if (threadIdx.x < 32) {
@@ -1127,11 +1141,11 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
               cbase[2 * ch + 1] = c1;
               a.ccnt[S.chunk_base + ch] = 0u;
               const unsigned prev = atom_add_acq_rel_u32(a.cnt + sid, 1u);
-              s_last = (prev == (unsigned)(nch - 1)) ? 2 : 0;
+              s_sys = (prev == (unsigned)(nch - 1)) ? 1 : 0;
             }
           }
           __syncthreads();
-          if (s_last == 2) {
+          if (s_sys) {
             double q0 = 0.0, q1 = 0.0;
             for (int tt = threadIdx.x; tt < nch; tt += blockDim.x) {
               q0 += __ldcg(cbase + 2 * tt);
@@ -1267,6 +1281,81 @@ __global__ void engine_continue_kernel(GridSync* gs, int64_t slot_cap, cudaGraph
     gs->pad[0] += 1;
     cudaGraphSetConditional(h, (live > 0 && err == 0 && (int64_t)slot < slot_cap) ? 1u : 0u);
   }
+}
+
+// Snake position of the item of rank j (in order of decreasing size) over
+// `grid` blocks: round r = j / grid runs blocks 0 .. grid - 1 when r is even
+// and grid - 1 .. 0 when it is odd; block b takes positions b, b + grid, ...
+__host__ __device__ __forceinline__ int64_t snake_pos(int64_t j, int grid) {
+  const int64_t r = j / grid, c = j % grid;
+  return r * grid + ((r & 1) ? grid - 1 - c : c);
+}
+
+// Between launches of a batch: the launch table dealt again over the systems
+// still running (the same order by size, the same snake), so that members
+// that finished leave neither holes nor idle blocks.  One block; the items
+// (ord_sys, ord_tile: every member's items in order of decreasing size) are
+// ranked among the live ones by a block-wide scan.  Which block runs an item
+// does not change its arithmetic.
+__global__ void __launch_bounds__(1024) redeal_kernel(GridSync* gs, const EngState* st0, const EngState* st1,
+                                                      const int32_t* __restrict__ ord_sys,
+                                                      const int32_t* __restrict__ ord_tile, int64_t items, int grid,
+                                                      int32_t nsys, int64_t cap, int32_t* item_sys,
+                                                      int32_t* item_tile) {
+  __shared__ int wsum[32];
+  __shared__ int64_t base;
+  const int slot = *(volatile int*)&gs->slot;
+  const EngState* cur = (slot & 1) ? st1 : st0;  // the states the next launch starts from
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < items; c0 += blockDim.x) {
+    const int64_t i = c0 + threadIdx.x;
+    int sid = -1, live = 0;
+    if (i < items) {
+      sid = __ldg(ord_sys + i);
+      if (sid < 0 || sid >= nsys) {
+        atomicCAS(&gs->err, 0, kErrTable);
+        sid = -1;
+      } else {
+        live = __ldcg(&cur[sid].phase) != PH_DONE ? 1 : 0;
+      }
+    }
+    // exclusive rank of this item among the chunk's live items
+    const unsigned bal = __ballot_sync(0xffffffffu, live);
+    const int below = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < wid) before += wsum[w];
+      total += wsum[w];
+    }
+    if (live) {
+      const int64_t pos = snake_pos(base + before + below, grid);
+      if (pos < cap) {
+        item_sys[pos] = sid;
+        item_tile[pos] = __ldg(ord_tile + i);
+      } else {
+        atomicCAS(&gs->err, 0, kErrTable);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+  // holes of the last round: the blocks it does not reach
+  const int64_t nl = base;
+  const int64_t rounds = (nl + grid - 1) / grid;
+  const int rem = (int)(nl - (rounds > 0 ? (rounds - 1) * grid : 0));  // items in the last round
+  if (rounds > 0 && rem < grid && rounds * grid <= cap) {
+    const int64_t r = rounds - 1;
+    for (int b = threadIdx.x; b < grid; b += blockDim.x) {
+      const bool hole = (r & 1) ? (b < grid - rem) : (b >= rem);
+      if (hole) item_sys[r * grid + b] = -1;
+    }
+  }
+  if (threadIdx.x == 0) gs->npos = (int)(rounds * grid <= cap ? rounds * grid : 0);
 }
 
 template <class VT, class GT, bool MIXED>
@@ -1564,7 +1653,7 @@ class EngineBatch {
     const int64_t rounds = (items + grid - 1) / grid;
     const int64_t npos = rounds * grid;
     if (npos >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
-    std::vector<int32_t> isys(npos, -1), itile(npos, 0);
+    std::vector<int32_t> isys(npos, -1), itile(npos, 0), osys, otile;
     {
       std::vector<int64_t> ord(items);
       std::vector<double> w(items);
@@ -1589,11 +1678,12 @@ class EngineBatch {
           owner[hs[i].item_base + v] = i;
           idx[hs[i].item_base + v] = v;
         }
+      osys.resize(items);
+      otile.resize(items);
       for (int64_t j = 0; j < items; ++j) {
-        const int64_t r = j / grid, c = j % grid;
-        const int64_t pos = r * grid + ((r & 1) ? grid - 1 - c : c);
-        isys[pos] = owner[ord[j]];
-        itile[pos] = idx[ord[j]];
+        const int64_t pos = snake_pos(j, grid);
+        isys[pos] = osys[j] = owner[ord[j]];
+        itile[pos] = otile[j] = idx[ord[j]];
       }
     }
     std::vector<EngState> hst(nsys);
@@ -1608,7 +1698,8 @@ class EngineBatch {
     const size_t off_cpart = off_cnt + al(sz_cnt), off_ccnt = off_cpart + al(sz_cpart);
     const size_t off_gs = off_ccnt + al(sz_ccnt), off_flags = off_gs + al(sizeof(GridSync));
     const size_t off_dep = off_flags + al(sizeof(unsigned) * items);
-    const size_t total = off_dep + al(sizeof(int32_t) * 2 * items);
+    const size_t off_ord = off_dep + al(sizeof(int32_t) * 2 * items);  // items by size: system, item
+    const size_t total = off_ord + 2 * al(sizeof(int32_t) * items);
     if ((rc = tab_.alloc(total, s_))) return rc;
     char* tb = tab_.as<char>();
     SPAI_CUDA(cudaMemsetAsync(tb, 0, total, s_));
@@ -1634,9 +1725,18 @@ class EngineBatch {
     SPAI_CUDA(cudaMemcpyAsync(tb + off_st1, hst.data(), sz_st, cudaMemcpyHostToDevice, s_));
     SPAI_CUDA(cudaMemcpyAsync(tb + off_is, isys.data(), sz_items, cudaMemcpyHostToDevice, s_));
     SPAI_CUDA(cudaMemcpyAsync(tb + off_it, itile.data(), sz_items, cudaMemcpyHostToDevice, s_));
+    if (items > 0) {
+      SPAI_CUDA(cudaMemcpyAsync(tb + off_ord, osys.data(), sizeof(int32_t) * items, cudaMemcpyHostToDevice, s_));
+      SPAI_CUDA(cudaMemcpyAsync(tb + off_ord + al(sizeof(int32_t) * items), otile.data(), sizeof(int32_t) * items,
+                                cudaMemcpyHostToDevice, s_));
+    }
+    ord_sys_ = reinterpret_cast<const int32_t*>(tb + off_ord);
+    ord_tile_ = reinterpret_cast<const int32_t*>(tb + off_ord + al(sizeof(int32_t) * items));
+    items_ = items;
     GridSync g0;
     memset(&g0, 0, sizeof(g0));
     g0.live = live;
+    g0.npos = (int)npos;
     SPAI_CUDA(cudaMemcpyAsync(tb + off_gs, &g0, sizeof(g0), cudaMemcpyHostToDevice, s_));
     // host copies must stay alive until the copies ran
     SPAI_CUDA(cudaStreamSynchronize(s_));
@@ -1725,8 +1825,33 @@ class EngineBatch {
     cpk.gridDim = dim3(1);
     cpk.blockDim = dim3(32);
     cpk.kernelParams = cargs;
+    cudaGraphNode_t prev = kn;
+    int32_t* item_sys = const_cast<int32_t*>(args_.item_sys);
+    int32_t* item_tile = const_cast<int32_t*>(args_.item_tile);
+    EngState* st0 = args_.st0;
+    EngState* st1 = args_.st1;
+    const EngState* cst0 = st0;
+    const EngState* cst1 = st1;
+    const int32_t* osys = ord_sys_;
+    const int32_t* otile = ord_tile_;
+    int64_t nit = items_;
+    int grid = grid_;
+    int32_t nsys = nsys_;
+    int64_t cap = args_.n_items;  // positions the table holds
+    void* rargs[] = {&gs, &cst0, &cst1, &osys, &otile, &nit, &grid, &nsys, &cap, &item_sys, &item_tile};
+    if (nsys_ > 1 && items_ > 0) {  // members finish at different times: deal the live ones again
+      cudaKernelNodeParams rk;
+      memset(&rk, 0, sizeof(rk));
+      rk.func = reinterpret_cast<void*>(&redeal_kernel);
+      rk.gridDim = dim3(1);
+      rk.blockDim = dim3(1024);
+      rk.kernelParams = rargs;
+      cudaGraphNode_t rn;
+      SPAI_CUDA(cudaGraphAddKernelNode(&rn, body, &kn, 1, &rk));
+      prev = rn;
+    }
     cudaGraphNode_t cn;
-    SPAI_CUDA(cudaGraphAddKernelNode(&cn, body, &kn, 1, &cpk));
+    SPAI_CUDA(cudaGraphAddKernelNode(&cn, body, &prev, 1, &cpk));
     SPAI_CUDA(cudaGraphInstantiate(&gr.e, gr.g, 0));
     if (ev0) SPAI_CUDA(cudaEventRecord(ev0, s_));
     SPAI_CUDA(cudaGraphLaunch(gr.e, s_));
@@ -1743,6 +1868,7 @@ class EngineBatch {
     count_launch(2 * gh.pad[0]);
     slots_ = gh.slot;
     live_ = gh.live;
+    if (gh.err == kErrTable) return set_error(SPAI_ERR_INVALID, "engine: a launch-table entry was out of range");
     if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
     return SPAI_OK;
   }
@@ -1771,6 +1897,7 @@ class EngineBatch {
     }
     slots_ = gh.slot;
     live_ = gh.live;
+    if (gh.err == kErrTable) return set_error(SPAI_ERR_INVALID, "engine: a launch-table entry was out of range");
     if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
     return SPAI_OK;
   }
@@ -1797,6 +1924,9 @@ class EngineBatch {
   int64_t max_iter_ = 0, slots_ = 0;
   DevMem tab_;
   EngArgs args_;
+  const int32_t* ord_sys_ = nullptr;   // every member's items in order of decreasing size
+  const int32_t* ord_tile_ = nullptr;
+  int64_t items_ = 0;
 };
 
 // ||b - A x|| / ||b|| for each system (float64, deterministic).
@@ -1880,7 +2010,9 @@ int engine_run(int nsys, SystemData* const* S, PrecondData* const* M, const doub
   }
   if ((rc = B.set_members(mem, grid_override))) return rc;
   const int64_t slot_cap = 8 * B.max_iter() + 64;
-  const int chunk = 3000;
+  // a batch returns to the re-deal every 128 slots (members finish at
+  // different times); one system alone keeps its table for 3000
+  const int chunk = nsys > 1 ? 128 : 3000;
   int launches = 0;
   double engine_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -2266,6 +2398,7 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
   GridSync g0;
   memset(&g0, 0, sizeof(g0));
   g0.live = 1;
+  g0.npos = items;  // item v at position v, no holes
   SPAI_CUDA(cudaMemsetAsync(base + off_zero, 0, off_vec - off_zero, s));
   SPAI_CUDA(cudaMemcpyAsync(base + off_sys, &e, sizeof(e), cudaMemcpyHostToDevice, s));
   SPAI_CUDA(cudaMemcpyAsync(base + off_st0, &st, sizeof(st), cudaMemcpyHostToDevice, s));
@@ -2316,6 +2449,7 @@ extern "C" int spai_pcg_solve_noalloc(const spai_csr* A, const spai_csr* G, cons
     SPAI_CUDA(cudaMemcpyAsync(&gh, args.gs, sizeof(gh), cudaMemcpyDeviceToHost, s));
     SPAI_CUDA(cudaStreamSynchronize(s));
     done_slots = gh.slot;
+    if (gh.err == kErrTable) return set_error(SPAI_ERR_INVALID, "engine: a launch-table entry was out of range");
     if (gh.err) return set_error(SPAI_ERR_TIMEOUT, "engine: a bounded device wait timed out");
     if (gh.live <= 0) break;
   }

@@ -374,7 +374,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch
 struct GridSync {
   unsigned count;  // blocks arrived
   unsigned gen;    // generation (counts in steps of 2); bit 0: the exit decided at the last barrier
-  int unused;
+  int npos;        // positions of the launch table in use (holes included)
   int err;         // SPAI_ERR_TIMEOUT when a wait gave up
   int live;        // systems still running
   int slot;        // slots executed so far (parity of double-buffered state)
