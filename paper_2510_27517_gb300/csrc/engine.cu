@@ -1056,6 +1056,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
 
   const int slot0 = *(volatile int*)&a.gs->slot;
   const int npos = *(volatile int*)&a.gs->npos;  // fixed for the launch (re-dealt only between launches)
+  bool skipped = false;  // the last item left without its closing block barrier
   int slots = 0;
   for (;;) {
     const int par = (slot0 + slots) & 1;
@@ -1066,32 +1067,50 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
     // steps (PH_P2F), whose items wait for the flags pass 0 published.  The
     // item at table position p runs in block p % grid in both passes; a
     // block finishes its pass-0 items before it waits in pass 1.
+    // `cur` changes within a slot only by finished systems, so the items of
+    // fused steps are the same in both passes: a block that met none in
+    // pass 0 has nothing to do in pass 1
+    bool any_fused = false;
     for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1 && !any_fused) break;
       int cached = -1;
       for (int it = blockIdx.x; it < npos; it += gridDim.x) {
         const int sid = __ldg(a.item_sys + it);
         if (sid < 0) continue;  // a hole of the last round
         const int v = __ldg(a.item_tile + it);
-        if (sid >= a.nsys || v < 0 || v >= a.sys[sid].nitems) {  // a corrupt table entry: flag it, skip it
+        if (sid >= a.nsys) {  // a corrupt table entry: flag it, skip it
           if (threadIdx.x == 0) atomicCAS(&a.gs->err, 0, kErrTable);
           continue;
         }
         if (sid != cached) {
-          // every thread has read the previous system's state (the skips
-          // below leave an item without the closing barrier)
-          __syncthreads();
+          // a skipped item below leaves without the closing barrier: wait
+          // until every warp has read the state it replaces
+          if (skipped) __syncthreads();
           if (threadIdx.x == 0) load_state(cur + sid, &s_st);
           __syncthreads();
           cached = sid;
+          skipped = false;
         }
         const int ph0 = s_st.phase;
-        if (ph0 == PH_DONE) continue;
+        if (ph0 == PH_DONE) {
+          skipped = true;
+          continue;
+        }
         const bool fused = ph0 == PH_P2F;
-        if (pass == 1 && !fused) continue;
+        any_fused |= fused;
+        if (pass == 1 && !fused) {
+          skipped = true;
+          continue;
+        }
         const int ph = fused ? (pass == 0 ? PH_P2 : PH_APPLY2) : ph0;
         const EngSys& S = a.sys[sid];
         const int m = phase_mat(ph);
         const int K = S.kgroups[m];
+        if (v < 0 || v >= S.nitems) {  // a corrupt table entry: flag it, skip it
+          if (threadIdx.x == 0) atomicCAS(&a.gs->err, 0, kErrTable);
+          skipped = true;
+          continue;
+        }
         const int g0 = v * K;
         int g1 = g0 + K;
         if (g1 > S.ntiles[m]) g1 = S.ntiles[m];
