@@ -193,6 +193,42 @@ def test_batched_equals_alone(spai_lib):
 
 
 @pytest.mark.parametrize("mixed", [False, True])
+def test_batch_over_many_rounds_equals_alone(spai_lib, mixed):
+    # one work item per row group (items_log2 -4): the batch holds several
+    # times more items than the grid has blocks, so every block runs items of
+    # several members per pass, dealt by size in a snake, and members that
+    # finish early are dealt out between launches; each member's iteration
+    # is bit-identical to its solve alone (where its own items take more than
+    # one round too)
+    spai = spai_lib
+    gdt = spai.F32 if mixed else spai.F64
+    prec = spai.PREC_MIXED if mixed else spai.PREC_F64
+    mats = [W.aniso2d(300, 30.0, 0.4), W.poisson2d(60), W.aniso2d(220, 5.0, 1.1), W.poisson2d(150),
+            W.aniso2d(40, 200.0, 2.5), W.aniso2d(180, 2.0, 0.2)]
+    blob = torch.tensor(W.gnn_random_weights(1, 4), device="cuda")
+    systems, preconds, bs, keep, alone = [], [], [], [], []
+    for i, A in enumerate(mats):
+        dA = upload(spai, A)
+        S = spai.system_create(dA)
+        S.set_schedule(items_log2=-4)
+        P = spai.build_pattern(dA, spai.PATTERN_FULL)
+        M = spai.gnn_precond(dA, P, torch.tensor(W.row_average_feature(A), device="cuda"), blob, d_node=1,
+                             g_dtype=gdt, eps=0.3)
+        b = torch.tensor(W.rhs_uniform(A.n, 300 + i), device="cuda")
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        alone.append((spai.system_solve(S, M, b, x, precision=prec), x.clone()))
+        systems.append(S), preconds.append(M), bs.append(b), keep.append((dA, P))
+    xs = [torch.zeros_like(b) for b in bs]
+    res = spai.pcg_solve_batched(systems, preconds, bs, xs, precision=prec)
+    iters = [r["iters"] for r in res]
+    assert max(iters) > 2 * min(iters)  # members finish at different times
+    for (ra, xa), rb, xb in zip(alone, res, xs):
+        assert rb["status"] == 0 and ra["status"] == 0
+        assert rb["iters"] == ra["iters"] and rb["outer_iters"] == ra["outer_iters"]
+        assert torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
 def test_sell_and_csr_members_in_one_launch(spai_lib, mixed):
     # a launch whose members all stream SELL-32 slices runs the kernel built
     # without the CSR ring; a batch that also holds a CSR system runs the full
