@@ -701,7 +701,7 @@ def run_ppt(args):
     torch.cuda.set_device(0)
     blob = W.gnn_random_weights(1, 4, seed=W.BASE_SEED + 100)
     systems, preconds, bs, keep, sizes = [], [], [], [], []
-    for i, (n, seed) in enumerate(W.ppt_batch(args.batch)):
+    for i, (n, seed) in enumerate(W.ppt_batch(args.ppt_batch)):
         A_h = W.ppt_synthetic(n, seed=seed)
         A = spai.CSRMatrix.from_numpy(A_h.n, A_h.rowptr, A_h.colidx, A_h.val)
         P, M = _gnn_for(spai, A, A_h, W.row_average_feature(A_h).astype(np.float32), blob, 1, spai.F32, args.eps)
@@ -735,14 +735,14 @@ def run_ppt(args):
     _, alone_ms = _timed(seq)
     ms = statistics.median(ts)
     iters = [r["iters"] for r in res]
-    line = _common_line(args, "solves/s to rtol 1e-8 (synthetic P P^T + eps I batch)", args.batch / (ms / 1e3),
+    line = _common_line(args, "solves/s to rtol 1e-8 (synthetic P P^T + eps I batch)", args.ppt_batch / (ms / 1e3),
                         "solves/s",
-                        {"workload": f"{args.batch} systems A = P P^T + 1e-4 I, n uniform [12000, 24000], P density "
+                        {"workload": f"{args.ppt_batch} systems A = P P^T + 1e-4 I, n uniform [12000, 24000], P density "
                                      f"3e-4, GNN-SPAI G (f32), eps {args.eps}, f32 PCG in f64 refinement",
                          "sum_nnz": sum(z for _, z in sizes)},
                         {"ms_per_batch": ms, "iters_min": min(iters), "iters_max": max(iters),
                          "iters_mean": statistics.mean(iters), "one_at_a_time_ms": alone_ms,
-                         "batch_speedup": alone_ms / ms, "ms_per_solve_alone_mean": alone_ms / args.batch})
+                         "batch_speedup": alone_ms / ms, "ms_per_solve_alone_mean": alone_ms / args.ppt_batch})
     return line
 
 
@@ -1194,6 +1194,7 @@ def main():
     ap.add_argument("--pair", type=int, default=-1, choices=[-1, 0, 1],
                     help="graph and probe: paired vectors off (0) / on (1); -1: the system's default")
     ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--ppt-batch", type=int, default=64, help="systems of the P P^T workload")
     ap.add_argument("--batch-side-hi", type=int, default=512)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--batch-items-log2", type=int, default=4,
