@@ -1417,9 +1417,9 @@ size_t engine_smem_bytes(bool mixed, bool csr_ring = true) {
 
 bool engine_groups_fit(int32_t max_row) { return max_row >= 1 && max_row <= kCap / 2; }
 
-// Groups per work item: items are handed to blocks round-robin, so pick the
-// K minimising  rounds * (K * t_group + t_item)  with rounds = ceil(items /
-// grid), t_item ~ 3 t_group of fixed per-item cost.  Depends only on the
+// Groups per work item: a system alone has its items dealt one per block per
+// round, so pick the K minimising  rounds * (K * t_group + t_item)  with
+// rounds = ceil(items / grid), t_item ~ 3 t_group of fixed per-item cost.  Depends only on the
 // system's group count and the kernel's co-resident grid.
 int engine_items_k(int ngroups, int grid) {
   if (ngroups <= 1 || grid <= 0) return 1;
