@@ -1030,11 +1030,15 @@ __device__ void transition(const EngSys& S, EngState& st, double q0, double q1, 
   }
 }
 
+// The state of one system into shared memory: one 8-byte word per lane of
+// the first half-warp, so the 128-byte line arrives in one warp-wide request
+// (every block reads the same line right after the grid barrier).
 __device__ __forceinline__ void load_state(const EngState* src, EngState* dst) {
-  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
-  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(EngState) / 8); ++i) d[i] = __ldcg(s + i);
+  constexpr int kWords = (int)(sizeof(EngState) / 8);
+  static_assert(kWords <= 32, "one word per lane");
+  if (threadIdx.x < kWords)
+    reinterpret_cast<unsigned long long*>(dst)[threadIdx.x] =
+        __ldcg(reinterpret_cast<const unsigned long long*>(src) + threadIdx.x);
 }
 
 template <class VT, class GT, bool MIXED, int KV>
@@ -1086,7 +1090,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(EngArgs a) {
           // a skipped item below leaves without the closing barrier: wait
           // until every warp has read the state it replaces
           if (skipped) __syncthreads();
-          if (threadIdx.x == 0) load_state(cur + sid, &s_st);
+          load_state(cur + sid, &s_st);
           __syncthreads();
           cached = sid;
           skipped = false;
