@@ -39,6 +39,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "deal.h"
 #include "internal.cuh"
 
 namespace spai {
@@ -1306,14 +1307,6 @@ __global__ void engine_continue_kernel(GridSync* gs, int64_t slot_cap, cudaGraph
   }
 }
 
-// Snake position of the item of rank j (in order of decreasing size) over
-// `grid` blocks: round r = j / grid runs blocks 0 .. grid - 1 when r is even
-// and grid - 1 .. 0 when it is odd; block b takes positions b, b + grid, ...
-__host__ __device__ __forceinline__ int64_t snake_pos(int64_t j, int grid) {
-  const int64_t r = j / grid, c = j % grid;
-  return r * grid + ((r & 1) ? grid - 1 - c : c);
-}
-
 // Between launches of a batch: the launch table dealt again over the systems
 // still running (the same order by size, the same snake), so that members
 // that finished leave neither holes nor idle blocks.  One block; the items
@@ -1673,12 +1666,10 @@ class EngineBatch {
     // sizes load every block about equally; holes of the last round hold
     // system -1.  Which block runs an item does not change its arithmetic.
     // One system alone in at most one round keeps item v at position v.
-    const int64_t rounds = (items + grid - 1) / grid;
-    const int64_t npos = rounds * grid;
+    const int64_t npos = deal_positions(items, grid);
     if (npos >= INT32_MAX) return set_error(SPAI_ERR_INVALID, "too many work items");
     std::vector<int32_t> isys(npos, -1), itile(npos, 0), osys, otile;
     {
-      std::vector<int64_t> ord(items);
       std::vector<double> w(items);
       for (int i = 0; i < nsys; ++i) {
         const EngSys& e = hs[i];
@@ -1690,11 +1681,10 @@ class EngineBatch {
             const int64_t g = std::min<int64_t>(e.kgroups[mm], (int64_t)e.ntiles[mm] - (int64_t)v * e.kgroups[mm]);
             if (g > 0 && e.ntiles[mm] > 0) wt += (double)g * ent[mm] / e.ntiles[mm];
           }
-          ord[e.item_base + v] = e.item_base + v;
           w[e.item_base + v] = wt;
         }
       }
-      std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return w[x] > w[y]; });
+      const std::vector<int64_t> ord = deal_order(w);
       std::vector<int32_t> owner(items), idx(items);
       for (int i = 0; i < nsys; ++i)
         for (int v = 0; v < hs[i].nitems; ++v) {
