@@ -293,10 +293,17 @@ def oracle_fsai_leg(args):
     print(json.dumps({"t_fsai_s": t_fsai, "t_pcg_s": t_pcg, "iters": ref.iters, "cores": 1}))
 
 
+# Iterations of the headline system measured on the GPU (grid, eps): 128^3
+# diffusion with the seeded random-init GNN G, mixed precision to rtol 1e-8.
+MEASURED_ITERS = {(128, 0.3): 150834}
+
+
 def iteration_model(args):
-    """The oracle's own iteration counts for the benchmark's G recipe at small
-    grids, fitted as k = c N^p and extrapolated to the benchmark grid (the
-    oracle cannot finish the full solve).  Returns (k, description)."""
+    """Iterations of one solve for the reference arm, which cannot finish the
+    full solve: the count measured on the GPU for this exact system where one
+    is recorded (MEASURED_ITERS), else the oracle's own iteration counts for
+    the benchmark's G recipe at small grids fitted as k = c N^p and
+    extrapolated to the benchmark grid.  Returns (k, description)."""
     import numpy as np
 
     import workloads as W
@@ -313,8 +320,15 @@ def iteration_model(args):
         its.append(r.iters)
     p, c = np.polyfit(np.log(sides), np.log(its), 1)
     k = int(round(math.exp(c) * args.grid ** p))
-    return k, (f"oracle iterations at {sides[0]}^3, {sides[1]}^3, {sides[2]}^3 = {its} fitted as k ~ N^{p:.2f}, "
-               f"extrapolated to {args.grid}^3")
+    fit = (f"oracle iterations at {sides[0]}^3, {sides[1]}^3, {sides[2]}^3 = {its} fitted as k ~ N^{p:.2f}, "
+           f"extrapolated to {args.grid}^3")
+    measured = MEASURED_ITERS.get((args.grid, args.eps))
+    if measured is not None:
+        # the coefficient field's contrast grows with the grid, so small grids
+        # say little about 128^3; the measured count of this exact system wins
+        return measured, (f"{measured} iterations: the GPU solve of this exact system (same A, G and b; "
+                          f"Algorithm 1 to rtol 1e-8) measured them; for comparison, {fit} gives {k}")
+    return k, fit
 
 
 # ---------------------------------------------------------------------------

@@ -102,3 +102,16 @@ def test_trained_weights_metadata_matches_the_blob():
     ev = meta["eval_pcg_f64_rtol1e-8"]
     small = [e for e in ev if e["N"] <= 24]
     assert small and all(e["trained"] < e["jacobi"] < e["plain_cg"] for e in small)
+
+
+def test_reference_iteration_count_at_the_headline_grid_is_the_measured_one():
+    # at 128^3 the small-grid fit is far off (the coefficient contrast grows
+    # with the grid); the arm uses the GPU's measured count and states both
+    b = _bench()
+
+    class A:
+        grid = 128
+        eps = 0.3
+    k, desc = b.iteration_model(A)
+    assert k == b.MEASURED_ITERS[(128, 0.3)] == 150834
+    assert "measured" in desc and "fitted as k ~ N^" in desc
