@@ -181,28 +181,34 @@ def _oracle_env():
     return env
 
 
-def cpu_leg(args):
-    """Times the float64 oracle on a bounded sample of the workload and scales
-    it to one solve: the GNN forward on the first 8 z-slabs of the grid
-    (scaled by stored entries) plus `samp` oracle PCG iterations on the full
-    system (scaled by the iteration count `k`).  With --cpu-check-x it also
-    computes, with the oracle, the float64 true residual of the x the GPU
-    benchmarked, and with --cpu-small-x the forward error of the GPU's solve
-    of the same generator at a small grid against the oracle's solution.
-    Prints one JSON object."""
-    import numpy as np
-
+def cpu_prepare(args, slabs: int = 8):
+    """The host workload and the oracle's GNN sub-problem (the first `slabs`
+    z-slabs of the grid), built once; not part of the timed sample."""
     import workloads as W
-    from oracle import gnn, pcg
 
     h = make_host_workload(args, 0)
-    A, v, blob, b = h["A"], h["v"], h["blob"], h["b"]
+    A = h["A"]
     N = args.grid
-    ns = min(A.n, 8 * N * N)
+    ns = min(A.n, slabs * N * N)
     m = int(A.rowptr[ns])
     keep = A.colidx[:m] < ns
+    import numpy as np
     rows = np.repeat(np.arange(ns), np.diff(A.rowptr[:ns + 1]))
     sub = W.coo_to_csr(ns, rows[keep], A.colidx[:m][keep], A.val[:m][keep])
+    return {"A": A, "v": h["v"], "blob": h["blob"], "b": h["b"], "ns": ns, "sub": sub}
+
+
+def cpu_sample(ctx, args, k: int, k_src: str, iters: int = 0):
+    """Times the float64 oracle on a bounded sample of the workload and scales
+    it to one solve: the GNN forward on the sub-problem (scaled by stored
+    entries) plus `iters` (default `args.cpu_iters`) oracle PCG iterations on
+    the full system (scaled by the iteration count k).  One thread (the
+    caller's BLAS setting).  Returns one dict."""
+    import numpy as np
+
+    from oracle import gnn, pcg
+
+    A, v, blob, b, ns, sub = ctx["A"], ctx["v"], ctx["blob"], ctx["b"], ctx["ns"], ctx["sub"]
     t0 = time.perf_counter()
     g_sub = gnn.gnn_forward(sub.n, sub.rowptr, sub.colidx, sub.val, v[:ns], blob)
     t_gnn_sub = time.perf_counter() - t0
@@ -211,17 +217,32 @@ def cpu_leg(args):
     # tiled (values do not change the cost of an iteration)
     g = np.resize(g_sub, A.nnz)
     apply = pcg.spai_apply(A.n, A.rowptr, A.colidx, g, args.eps)
-    samp = args.cpu_iters
+    samp = iters or args.cpu_iters
     t0 = time.perf_counter()
     res = pcg.pcg(A.n, A.rowptr, A.colidx, A.val, b, apply, rtol=0.0, max_iter=samp, replace_period=50)
     t_it = (time.perf_counter() - t0) / max(1, res.iters)
-    k = args.cpu_k
     t_solve = t_gnn + k * t_it
-    out = {"t_gnn_s": t_gnn, "t_iter_s": t_it, "k": k, "t_solve_s": t_solve, "value": 1.0 / t_solve, "cores": 1,
-           "host_cores": os.cpu_count(),
-           "sample": f"oracle GNN forward on {ns} of {A.n} rows ({sub.nnz} entries, scaled by nnz) "
-                     f"+ {res.iters} oracle PCG iterations on the full system, scaled to k={k} ({args.cpu_k_src})",
-           "sample_wall_s": t_gnn_sub + t_it * res.iters}
+    return {"t_gnn_s": t_gnn, "t_iter_s": t_it, "k": k, "t_solve_s": t_solve, "value": 1.0 / t_solve, "cores": 1,
+            "host_cores": os.cpu_count(),
+            "sample": f"oracle GNN forward on {ns} of {A.n} rows ({sub.nnz} entries, scaled by nnz) "
+                      f"+ {res.iters} oracle PCG iterations on the full system, scaled to k={k} ({k_src})",
+            "sample_wall_s": t_gnn_sub + t_it * res.iters}
+
+
+def cpu_leg(args):
+    """The oracle's bounded sample (cpu_sample) in a process of its own, one
+    thread.  With --cpu-check-x it also computes, with the oracle, the
+    float64 true residual of the x the GPU benchmarked, and with
+    --cpu-small-x the forward error of the GPU's solve of the same generator
+    at a small grid against the oracle's solution.  Prints one JSON object."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import gnn, pcg
+
+    ctx = cpu_prepare(args)
+    A, blob, b = ctx["A"], ctx["blob"], ctx["b"]
+    out = cpu_sample(ctx, args, args.cpu_k, args.cpu_k_src)
     if args.cpu_check_x:
         x = np.load(args.cpu_check_x)
         out["oracle_true_rel_res"] = pcg.true_rel_residual(A.n, A.rowptr, A.colidx, A.val, x, b)
@@ -1138,11 +1159,11 @@ def run_probe(args):
 # reference arm: the float64 CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args):
-    """The float64 CPU oracle on the headline workload: each step times the
-    oracle's GNN forward on a bounded slice and a few PCG iterations on the
-    full system (one thread), scaled to one solve with the iteration count
-    that iteration_model() measures with the oracle at small grids and
-    extrapolates (fitted once per run)."""
+    """The float64 CPU oracle on the headline workload, in this process with
+    one BLAS thread: the workload is built once, then each step times the
+    oracle's GNN forward on the first two z-slabs and three PCG iterations on
+    the full system, scaled to one solve with the iteration count of
+    iteration_model() (fitted once per run)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -1151,16 +1172,21 @@ def run_reference(args):
     t_model = time.perf_counter() - t0
     vals = []
     last = None
-    for _ in range(args.warmup):
-        run_cpu_leg(args, k, k_src)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        last = run_cpu_leg(args, k, k_src)
-        if "error" in last:
-            print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + last["error"][-200:]}))
-            return
-        vals.append(last["value"])
-    wall = time.perf_counter() - t0
+    try:
+        # the workload, built once (not a timed part of a solve); each step a
+        # smaller sample than the GPU arm's one-off baseline, so that the
+        # driver's many steps end within minutes
+        ctx = cpu_prepare(args, args.ref_slabs)
+        for _ in range(args.warmup):
+            cpu_sample(ctx, args, k, k_src, args.ref_iters)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            last = cpu_sample(ctx, args, k, k_src, args.ref_iters)
+            vals.append(last["value"])
+        wall = time.perf_counter() - t0
+    except Exception as e:  # noqa: BLE001
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle run failed: {type(e).__name__}: {e}"[:300]}))
+        return
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
@@ -1235,6 +1261,8 @@ def main():
     ap.add_argument("--cpu-k", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-k-src", default="", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=6, help=argparse.SUPPRESS)
+    ap.add_argument("--ref-slabs", type=int, default=2, help=argparse.SUPPRESS)
+    ap.add_argument("--ref-iters", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-check-x", default="", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-small-x", default="", help=argparse.SUPPRESS)
     ap.add_argument("--fsai-leg", action="store_true", help=argparse.SUPPRESS)
@@ -1247,6 +1275,9 @@ def main():
     elif args.probe:
         run_probe(args)
     elif args.impl == "reference":
+        # the oracle runs in this process: one BLAS thread, set before numpy loads
+        os.environ.update({v: "1" for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                            "NUMEXPR_NUM_THREADS")})
         run_reference(args)
     elif args.workload in ("graph", "batch", "serve", "ppt", "fsai", "trained", "elastic"):
         fn = {"graph": run_graph, "batch": run_batch, "serve": run_serve, "ppt": run_ppt, "fsai": run_fsai,
