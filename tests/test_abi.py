@@ -50,3 +50,28 @@ def test_version_and_error_strings_without_gpu():
     L.spai_build_pattern.restype = ctypes.c_int
     assert L.spai_build_pattern(None, 0, None, None) == -1
     assert L.spai_last_error()
+
+
+def test_binding_struct_layouts_match_the_header():
+    # every struct the binding passes by pointer: the same size and the same
+    # offset for every field, from a C program built against include/spai.h
+    import tempfile
+    from paper_2510_27517_gb300 import spai as B
+    pairs = {"spai_csr": B._CSR, "spai_gnn_weights": B._GNNW, "spai_pcg_opts": B._Opts,
+             "spai_pcg_result": B._Res, "spai_schedule": B._Sched, "spai_adamw_cfg": B._AdamW,
+             "spai_system_layout": B._Layout, "spai_serve_cfg": B._ServeCfg, "spai_completion": B._Completion}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "spai.h"', "int main(void) {"]
+    want = []
+    for cname, S in pairs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(S))
+        for fname, _ in S._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append(getattr(S, fname).offset)
+    lines += ["  return 0;", "}"]
+    d = tempfile.mkdtemp(prefix="abi_layout_")
+    src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+    open(src, "w").write("\n".join(lines) + "\n")
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+    got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
